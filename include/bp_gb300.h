@@ -1,0 +1,164 @@
+/*
+ * bp_gb300 -- motion-compensated cone-beam backprojection and its analytic
+ * vector-Jacobian products on NVIDIA GB300 (sm_103a).
+ *
+ * The operations follow arXiv 2401.09283 (Thies et al., "A gradient-based
+ * approach to fast and accurate head motion compensation in cone-beam CT"):
+ *   - Eq. 1   rigid motion composition  Phat_j = P_j T(theta_j);
+ *   - Eq. 3   voxel-driven backprojection I(p) = sum_j d_j(g(Phat_j p~));
+ *   - Eqs. 4-5 the derivative of a backprojected value with respect to the
+ *             twelve entries of Phat_j, evaluated only as vector-Jacobian
+ *             products (Sec. II-B.2, last paragraph);
+ *   - Eq. 2   the chain rule down to the six motion parameters per view;
+ *   - Eq. 6   gradient descent with an exponentially decaying step.
+ *
+ * Conventions shared by every call:
+ *   - world coordinates in mm.  Voxel (i,j,k) sits at origin + (i,j,k)*spacing
+ *     and volumes are stored [nz][ny][nx], x fastest, float32, contiguous;
+ *   - projections are stored [nviews][nv][nu] with element strides
+ *     row_stride (between detector rows) and view_stride (between views);
+ *     u is the fastest axis; integer detector coordinates are pixel centres;
+ *     samples outside the detector read zero (zero padding);
+ *   - projection matrices are 3x4 row-major float64, (u,v,w) = P (x,y,z,1);
+ *     a view whose w <= 0 at a voxel contributes nothing there;
+ *   - motion parameters theta_j = (tx,ty,tz [mm], rx,ry,rz [rad]) define
+ *     T = [[R t],[0 1]] with R = Rz(rz) Ry(ry) Rx(rx), rotation about the
+ *     world origin (the isocenter);
+ *   - with BP_WEIGHT_FDK each sample is weighted c_j * (sid / w)^2, with
+ *     BP_WEIGHT_NONE by c_j alone (the paper's Eq. 3 has c_j = 1).
+ *
+ * Memory and ownership: every array argument is caller-owned and may be
+ * either device memory or host memory (pageable or pinned); the library
+ * tells them apart with cudaPointerGetAttributes.  Host inputs are copied to
+ * a device staging area owned by the context; host outputs are copied back
+ * and the call synchronises its stream before returning.  With only device
+ * pointers, calls are asynchronous on `stream` (a cudaStream_t, NULL for the
+ * legacy default stream).  The library never frees caller memory.
+ *
+ * Errors: every call returns a bp_status.  Invalid arguments are reported
+ * before any work is queued; CUDA launch or copy failures return
+ * BP_ERR_CUDA.  bp_last_error() gives a message for the last failure on the
+ * context.  Nothing in the library aborts, traps or spins without a bound.
+ *
+ * Thread safety: a context may be used by one host thread at a time.
+ */
+#ifndef BP_GB300_H
+#define BP_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BP_OK = 0,
+  BP_ERR_INVALID_ARG = -1,
+  BP_ERR_OOM = -2,
+  BP_ERR_CUDA = -3,
+  BP_ERR_UNSUPPORTED = -4,
+  BP_ERR_TIMEOUT = -5,
+  BP_ERR_CANCELLED = -6
+} bp_status;
+
+typedef enum { BP_F32 = 0, BP_F16 = 1, BP_BF16 = 2 } bp_dtype;
+
+/* Eq. 3 literally (NONE) or with the FDK distance weight (sid/w)^2. */
+typedef enum { BP_WEIGHT_NONE = 0, BP_WEIGHT_FDK = 1 } bp_weight;
+
+/* How g_u, g_v of Eq. 4 are obtained: CENTRAL = bilinear interpolation of
+ * gradient images made by central differences (second order in the
+ * interior, one-sided first order on the two edge pixels), as Sec. II-B.2
+ * describes; BILINEAR_EXACT = the exact partial derivatives of the bilinear
+ * interpolant (the true derivative of Eq. 3, used for gradient checks). */
+typedef enum { BP_DERIV_CENTRAL = 0, BP_DERIV_BILINEAR_EXACT = 1 } bp_deriv;
+
+typedef struct {
+  int nx, ny, nz;
+  double spacing[3]; /* mm */
+  double origin[3];  /* centre of voxel (0,0,0), mm */
+} bp_vol_desc;
+
+typedef struct {
+  int nu, nv, nviews;
+  int dtype;                   /* bp_dtype */
+  long long row_stride;        /* elements between detector rows (>= nu) */
+  long long view_stride;       /* elements between views (>= nv*row_stride) */
+  const float* view_scale;     /* optional per-view dequantisation scale,
+                                  value = scale[j] * stored; NULL = 1 */
+  double sid;                  /* source-isocenter distance, mm (FDK weight) */
+} bp_proj_desc;
+
+typedef struct bp_ctx bp_ctx;
+
+/* Create a context bound to CUDA device `device`.  The context owns only
+ * workspace (per-view tables, gradient images, partial sums, staging).
+ * Returns BP_ERR_INVALID_ARG for a bad device, BP_ERR_CUDA if the device
+ * cannot be used (including a device that is not sm_103). */
+int bp_ctx_create(int device, bp_ctx** out);
+void bp_ctx_destroy(bp_ctx* ctx);
+/* Message of the last failure on ctx ("" if none); valid until the next call. */
+const char* bp_last_error(const bp_ctx* ctx);
+/* Bytes of device workspace currently held by the context. */
+long long bp_ctx_workspace_bytes(const bp_ctx* ctx);
+
+/* Eq. 1 for every view: Phat[j] = P[j] T(motion[j]) (float64, [V][12]).
+ * motion may be NULL (identity; Phat is then P bit for bit). */
+int bp_compose(bp_ctx* ctx, int nviews, const double* P, const double* motion, double* Phat,
+               void* stream);
+
+/* Eq. 3: vol[k][j][i] = sum_j c_j * omega_j * d_j(u/w, v/w) with
+ * (u,v,w) = P_j T(motion_j) (x,y,z,1), bilinear interpolation, zero padding.
+ *   proj         projections, layout and dtype per pdesc;
+ *   P            float64 [V][12] calibrated matrices;
+ *   motion       float64 [V][6] or NULL (identity);
+ *   view_weight  float64 [V] (c_j) or NULL (all 1);
+ *   weight       bp_weight; FDK uses pdesc->sid;
+ *   vol          float32 output, overwritten.
+ * Accumulation is FP32 per voxel; coordinates are computed relative to an
+ * FP64 anchor per tile of voxels and view.  Deterministic. */
+int bp_forward(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, const double* P,
+               const double* motion, const double* view_weight, int weight,
+               const bp_vol_desc* vdesc, float* vol, void* stream);
+
+/* Vector-Jacobian products of bp_forward for an upstream gradient dL_dvol
+ * (float32, volume layout):
+ *   dL_dmotion  float64 [V][6]: Eq. 4 per voxel-view, summed per view
+ *               (FP32 within a tile, FP64 across tiles, deterministic), then
+ *               chained through Eq. 1 (Eq. 2);
+ *   dL_dPhat    float64 [V][12]: the per-view sum of Eq. 4 itself, i.e. the
+ *               gradient with respect to Phat_j = P_j T(motion_j);
+ *   dL_dproj    float32 [V][nv][nu] (contiguous): the adjoint of Eq. 3 in
+ *               the data, overwritten (FP32 atomics: not bitwise
+ *               deterministic).
+ * Any output may be NULL to skip it (dL_dmotion needs motion or treats it as
+ * zero).  With BP_WEIGHT_FDK the derivative of (sid/w)^2 is included. */
+int bp_vjp(bp_ctx* ctx, const float* dL_dvol, const void* proj, const bp_proj_desc* pdesc,
+           const double* P, const double* motion, const double* view_weight, int weight,
+           int deriv, const bp_vol_desc* vdesc, double* dL_dmotion, double* dL_dPhat,
+           float* dL_dproj, void* stream);
+
+/* Sharpness loss of a volume (stands in for the learned quality metric of
+ * Sec. II-B.3): L = -(1/K) sum over the three axes of the squared forward
+ * differences of all voxel pairs inside the volume, K = nx*ny*nz.
+ *   loss     float64 scalar output (host or device);
+ *   dL_dvol  float32 volume output (may be NULL).
+ * The FP64 sum is deterministic. */
+int bp_sharpness(bp_ctx* ctx, const float* vol, const bp_vol_desc* vdesc, double* loss,
+                 float* dL_dvol, void* stream);
+
+/* Optimiser steps on theta float64 [V][6] in place (device or host).
+ * Eq. 6: theta -= s0 * t^n * grad.  Adam: standard bias-corrected Adam with
+ * iteration counter n >= 1 and moments m1, m2 ([V][6], caller-owned, start
+ * at zero).  With gauge != 0 the per-parameter mean over views is removed
+ * afterwards (a rigid motion common to all views only moves the volume and
+ * is not identifiable by an image-quality loss). */
+int bp_gd_step(bp_ctx* ctx, int nviews, double* theta, const double* grad, double s0, double t,
+               int n, int gauge, void* stream);
+int bp_adam_step(bp_ctx* ctx, int nviews, double* theta, const double* grad, double* m1,
+                 double* m2, double lr, double beta1, double beta2, double eps, int n, int gauge,
+                 void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BP_GB300_H */

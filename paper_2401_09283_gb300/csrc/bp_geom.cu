@@ -1,0 +1,318 @@
+// FP64 per-view kernels (motion composition of Eq. 1, the cross-tile
+// reduction and chain rule of Eq. 2), the sharpness loss and the optimiser
+// updates (Eq. 6 and Adam).  None of these is on the voxel-view hot loop;
+// all are deterministic (fixed summation order, no atomics).
+#include "bp_internal.cuh"
+
+namespace bpk {
+
+// ---------------------------------------------------------------- rigid motion
+
+// R = Rz(rz) Ry(ry) Rx(rx) (row-major 3x3), or its derivative with respect
+// to one angle when dax = 0, 1, 2 (x, y, z).
+__device__ static void rot_zyx(const double* th, int dax, double R[9]) {
+  double sx, cx, sy, cy, sz, cz;
+  sincos(th[3], &sx, &cx);
+  sincos(th[4], &sy, &cy);
+  sincos(th[5], &sz, &cz);
+  double X[9] = {1, 0, 0, 0, cx, -sx, 0, sx, cx};
+  double Y[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy};
+  double Z[9] = {cz, -sz, 0, sz, cz, 0, 0, 0, 1};
+  if (dax == 0) {
+    double D[9] = {0, 0, 0, 0, -sx, -cx, 0, cx, -sx};
+    for (int e = 0; e < 9; ++e) X[e] = D[e];
+  } else if (dax == 1) {
+    double D[9] = {-sy, 0, cy, 0, 0, 0, -cy, 0, -sy};
+    for (int e = 0; e < 9; ++e) Y[e] = D[e];
+  } else if (dax == 2) {
+    double D[9] = {-sz, -cz, 0, cz, -sz, 0, 0, 0, 0};
+    for (int e = 0; e < 9; ++e) Z[e] = D[e];
+  }
+  double ZY[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      ZY[3 * r + c] = Z[3 * r] * Y[c] + Z[3 * r + 1] * Y[3 + c] + Z[3 * r + 2] * Y[6 + c];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      R[3 * r + c] = ZY[3 * r] * X[c] + ZY[3 * r + 1] * X[3 + c] + ZY[3 * r + 2] * X[6 + c];
+}
+
+// M (3x4) = P (3x4) * [[R t],[0 1]] (rigid 4x4 given by R and t).
+__device__ static void p_times_rigid(const double* P, const double R[9], const double t[3],
+                                     double tw, double* M) {
+  for (int r = 0; r < 3; ++r) {
+    const double* p = P + 4 * r;
+    for (int c = 0; c < 3; ++c) M[4 * r + c] = p[0] * R[c] + p[1] * R[3 + c] + p[2] * R[6 + c];
+    M[4 * r + 3] = p[0] * t[0] + p[1] * t[1] + p[2] * t[2] + p[3] * tw;
+  }
+}
+
+// One thread per view: Phat = P T(theta) (Eq. 1), then P' = Phat A.
+__global__ void compose_kernel(const double* __restrict__ P, const double* __restrict__ theta,
+                               const double* __restrict__ vw, const float* __restrict__ vscale,
+                               int V, int fdk, double sid, VolInfo vi, ViewGeom* __restrict__ geom,
+                               double* __restrict__ Phat) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= V) return;
+  double Ph[12];
+  if (theta) {
+    double R[9];
+    rot_zyx(theta + 6 * j, -1, R);
+    p_times_rigid(P + 12 * j, R, theta + 6 * j, 1.0, Ph);
+  } else {
+    for (int e = 0; e < 12; ++e) Ph[e] = P[12 * j + e];
+  }
+  if (Phat)
+    for (int e = 0; e < 12; ++e) Phat[12 * j + e] = Ph[e];
+  if (!geom) return;
+  ViewGeom g;
+  for (int r = 0; r < 3; ++r) {
+    const double* p = Ph + 4 * r;
+    // A = [[sx 0 0 tx],[0 sy 0 ty],[0 0 sz tz],[0 0 0 1]]
+    g.P[4 * r + 0] = p[0] * vi.A[0];
+    g.P[4 * r + 1] = p[1] * vi.A[5];
+    g.P[4 * r + 2] = p[2] * vi.A[10];
+    g.P[4 * r + 3] = p[0] * vi.A[3] + p[1] * vi.A[7] + p[2] * vi.A[11] + p[3];
+  }
+  double c = vw ? vw[j] : 1.0;
+  g.wgt = fdk ? c * sid * sid : c;
+  g.scale = vscale ? (double)vscale[j] : 1.0;
+  geom[j] = g;
+}
+
+cudaError_t launch_compose(const double* P, const double* theta, const double* view_weight,
+                           const float* view_scale, int V, int fdk, double sid,
+                           const VolInfo& vi, ViewGeom* geom, double* Phat, cudaStream_t s) {
+  if (V <= 0) return cudaSuccess;
+  compose_kernel<<<(V + 127) / 128, 128, 0, s>>>(P, theta, view_weight, view_scale, V, fdk, sid,
+                                                  vi, geom, Phat);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- cross-tile reduction + chain
+
+// Block j: dL/dP' for view j as the FP64 sum over tiles of the tile records
+// (each record is in its tile's anchored, centred frame and is mapped back to
+// the index frame first), then dL/dPhat = dL/dP' A^T and
+// dL/dtheta_m = < dL/dPhat , P dT/dtheta_m > (Eq. 2 through Eq. 1).
+__global__ void reduce_chain_kernel(const float* __restrict__ partials, int ntiles, VolInfo vi,
+                                    const double* __restrict__ P, const double* __restrict__ theta,
+                                    int V, double* __restrict__ dPhat, double* __restrict__ dth) {
+  __shared__ double red[12][256];
+  const int j = blockIdx.x;
+  const int tid = threadIdx.x;
+  double acc[12];
+  for (int e = 0; e < 12; ++e) acc[e] = 0.0;
+  for (int c = tid; c < ntiles; c += blockDim.x) {
+    const float* rec = partials + ((size_t)j * ntiles + c) * PSLOTS;
+    int tx = c % vi.tiles_x;
+    int ty = (c / vi.tiles_x) % vi.tiles_y;
+    int tz = c / (vi.tiles_x * vi.tiles_y);
+    double qc[3] = {tx * TX + 0.5 * (TX - 1) - vi.cx, ty * TY + 0.5 * (TY - 1) - vi.cy,
+                    tz * vi.zb + 0.5 * (vi.zb - 1) - vi.cz};
+    double G[12];
+    for (int r = 0; r < 3; ++r) {
+      double s = rec[4 * r + 3];
+      for (int k = 0; k < 3; ++k) G[4 * r + k] = (double)rec[4 * r + k] + s * qc[k];
+      G[4 * r + 3] = s;
+    }
+    double au = rec[12], av = rec[13];
+    for (int k = 0; k < 4; ++k) G[8 + k] -= au * G[k] + av * G[4 + k];
+    for (int e = 0; e < 12; ++e) acc[e] += G[e];
+  }
+  for (int e = 0; e < 12; ++e) red[e][tid] = acc[e];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (tid < w)
+      for (int e = 0; e < 12; ++e) red[e][tid] += red[e][tid + w];
+    __syncthreads();
+  }
+  if (tid != 0) return;
+  double Gp[12], Gh[12];
+  for (int e = 0; e < 12; ++e) Gp[e] = red[e][0];
+  const double sxyz[3] = {vi.A[0], vi.A[5], vi.A[10]};
+  const double txyz[3] = {vi.A[3], vi.A[7], vi.A[11]};
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) Gh[4 * r + c] = Gp[4 * r + c] * sxyz[c] + Gp[4 * r + 3] * txyz[c];
+    Gh[4 * r + 3] = Gp[4 * r + 3];
+  }
+  if (dPhat)
+    for (int e = 0; e < 12; ++e) dPhat[12 * j + e] = Gh[e];
+  if (!dth) return;
+  const double zero6[6] = {0, 0, 0, 0, 0, 0};
+  const double* th = theta ? theta + 6 * j : zero6;
+  const double* Pj = P + 12 * j;
+  for (int m = 0; m < 6; ++m) {
+    double J[12];
+    if (m < 3) {
+      // dT/dt_m: zero rotation block, unit vector in the translation column
+      const double Rz0[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      double t[3] = {0, 0, 0};
+      t[m] = 1.0;
+      p_times_rigid(Pj, Rz0, t, 0.0, J);
+    } else {
+      double dR[9];
+      const double t0[3] = {0, 0, 0};
+      rot_zyx(th, m - 3, dR);
+      p_times_rigid(Pj, dR, t0, 0.0, J);
+    }
+    double s = 0.0;
+    for (int e = 0; e < 12; ++e) s += Gh[e] * J[e];
+    dth[6 * j + m] = s;
+  }
+}
+
+cudaError_t launch_reduce_chain(const float* partials, int ntiles, const VolInfo& vi,
+                                const double* P, const double* theta, int V, double* dL_dPhat,
+                                double* dL_dtheta, cudaStream_t s) {
+  if (V <= 0) return cudaSuccess;
+  reduce_chain_kernel<<<V, 256, 0, s>>>(partials, ntiles, vi, P, theta, V, dL_dPhat, dL_dtheta);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- sharpness loss
+
+constexpr int SH_THREADS = 256;
+
+int sharpness_blocks(long long nvox) {
+  long long b = (nvox + SH_THREADS - 1) / SH_THREADS;
+  if (b > 4096) b = 4096;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// L = -(1/K) sum_pairs (I[y]-I[x])^2 over forward neighbours y = x + e_a
+// inside the volume; dL/dI[x] = (2/K) sum over the valid neighbours n of x
+// (I[n] - I[x]).  Per-block FP64 partial sums in a fixed order.
+__global__ void sharpness_kernel(const float* __restrict__ vol, int nx, int ny, int nz,
+                                 double* __restrict__ block_sums, float* __restrict__ grad) {
+  __shared__ double red[SH_THREADS];
+  const long long nvox = (long long)nx * ny * nz;
+  const double K = (double)nvox;
+  const float g2 = (float)(2.0 / K);
+  double acc = 0.0;
+  const long long nxy = (long long)nx * ny;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < nvox;
+       x += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(x % nx);
+    int j = (int)((x / nx) % ny);
+    int k = (int)(x / nxy);
+    float c = vol[x];
+    float gsum = 0.0f;
+    if (i + 1 < nx) {
+      float d = vol[x + 1] - c;
+      acc += (double)d * d;
+      gsum += d;
+    }
+    if (j + 1 < ny) {
+      float d = vol[x + nx] - c;
+      acc += (double)d * d;
+      gsum += d;
+    }
+    if (k + 1 < nz) {
+      float d = vol[x + nxy] - c;
+      acc += (double)d * d;
+      gsum += d;
+    }
+    if (grad) {
+      if (i > 0) gsum += vol[x - 1] - c;
+      if (j > 0) gsum += vol[x - nx] - c;
+      if (k > 0) gsum += vol[x - nxy] - c;
+      grad[x] = g2 * gsum;
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = SH_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = red[0];
+}
+
+__global__ void sharpness_finish_kernel(const double* __restrict__ block_sums, int nb, double K,
+                                        double* __restrict__ loss) {
+  __shared__ double red[SH_THREADS];
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += block_sums[b];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = SH_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = -red[0] / K;
+}
+
+cudaError_t launch_sharpness(const float* vol, int nx, int ny, int nz, double* block_sums,
+                             int max_blocks, double* loss, float* grad, cudaStream_t s) {
+  long long nvox = (long long)nx * ny * nz;
+  int nb = sharpness_blocks(nvox);
+  if (nb > max_blocks) nb = max_blocks;
+  sharpness_kernel<<<nb, SH_THREADS, 0, s>>>(vol, nx, ny, nz, block_sums, grad);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  sharpness_finish_kernel<<<1, SH_THREADS, 0, s>>>(block_sums, nb, (double)nvox, loss);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ optimisers
+
+// Subtract the per-parameter mean over views (fixed-order sums).
+__device__ static void remove_mean(int V, double* theta) {
+  __shared__ double red[256];
+  __shared__ double mean;
+  for (int m = 0; m < 6; ++m) {
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < V; j += blockDim.x) acc += theta[6 * j + m];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) mean = red[0] / V;
+    __syncthreads();
+    for (int j = threadIdx.x; j < V; j += blockDim.x) theta[6 * j + m] -= mean;
+    __syncthreads();
+  }
+}
+
+__global__ void gd_kernel(int V, double* theta, const double* grad, double step, int gauge) {
+  for (int e = threadIdx.x; e < 6 * V; e += blockDim.x) theta[e] -= step * grad[e];
+  __syncthreads();
+  if (gauge) remove_mean(V, theta);
+}
+
+__global__ void adam_kernel(int V, double* theta, const double* grad, double* m1, double* m2,
+                            double lr, double b1, double b2, double eps, double c1, double c2,
+                            int gauge) {
+  for (int e = threadIdx.x; e < 6 * V; e += blockDim.x) {
+    double g = grad[e];
+    double a = b1 * m1[e] + (1.0 - b1) * g;
+    double b = b2 * m2[e] + (1.0 - b2) * g * g;
+    m1[e] = a;
+    m2[e] = b;
+    theta[e] -= lr * (a / c1) / (sqrt(b / c2) + eps);
+  }
+  __syncthreads();
+  if (gauge) remove_mean(V, theta);
+}
+
+cudaError_t launch_gd(int V, double* theta, const double* grad, double s0, double t, int n,
+                      int gauge, cudaStream_t s) {
+  if (V <= 0) return cudaSuccess;
+  gd_kernel<<<1, 256, 0, s>>>(V, theta, grad, s0 * pow(t, (double)n), gauge);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(int V, double* theta, const double* grad, double* m1, double* m2,
+                        double lr, double b1, double b2, double eps, int n, int gauge,
+                        cudaStream_t s) {
+  if (V <= 0) return cudaSuccess;
+  double c1 = 1.0 - pow(b1, (double)n), c2 = 1.0 - pow(b2, (double)n);
+  adam_kernel<<<1, 256, 0, s>>>(V, theta, grad, m1, m2, lr, b1, b2, eps, c1, c2, gauge);
+  return cudaGetLastError();
+}
+
+}  // namespace bpk

@@ -1,0 +1,100 @@
+// Internal declarations of the bp_gb300 library (CUDA, sm_103a).
+//
+// Frames used by the kernels (all derived from the caller's inputs in FP64):
+//   index frame  voxel coordinates relative to the volume centre,
+//                q = (i - cx, j - cy, k - cz), c = (n-1)/2 per axis;
+//   P'           = Phat * A, where A maps the index frame to world mm, so
+//                (u, v, w) = P' (q, 1) with (u/w, v/w) in absolute pixels;
+//   anchored     per (tile of voxels, view) the integer pixel (au, av)
+//                nearest the tile centre's projection is subtracted:
+//                rows R_u = P'_0 - au P'_2, R_v = P'_1 - av P'_2, R_w = P'_2,
+//                and the tile centre qc is factored out, q = qc + dq.
+//                The FP32 inner loops see only small numbers (|u/w| of a
+//                few tens of pixels, |dq| of a few voxels), so detector
+//                positions keep ~1e-6 px precision up to 1240-px detectors.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace bpk {
+
+// Volume-major tiling: a CTA owns TX x TY voxel columns of ZB voxels each.
+constexpr int TX = 16;
+constexpr int TY = 16;
+constexpr int NT = TX * TY;   // threads per CTA
+constexpr int VB = 32;        // views per FP64 set-up batch
+constexpr int PSLOTS = 16;    // floats per (tile, view) partial record
+
+// Per view, written by compose_kernel.
+struct ViewGeom {
+  double P[12];   // P' = P T(theta) A   (index frame -> absolute pixels)
+  double wgt;     // c_j * (FDK ? sid^2 : 1)
+  double scale;   // per-view dequantisation scale (1 for float32 data)
+};
+
+// Per (tile, view), in shared memory.
+struct TileView {
+  float U0, V0, W0;   // anchored homogeneous coordinates at the tile centre
+  float ru[3];        // d(u_rel)/d(dq)
+  float rv[3];
+  float rw[3];
+  int au, av;         // anchor pixel
+  float wgt;          // wgt * scale (FP32)
+  int mode;           // MODE_*
+};
+
+enum { MODE_SKIP = 0, MODE_INTERIOR = 1, MODE_EDGE = 2 };
+
+struct VolInfo {
+  int nx, ny, nz;
+  int tiles_x, tiles_y, tiles_z;
+  int zb;
+  double cx, cy, cz;  // (n-1)/2
+  double A[12];       // index frame -> world (3x4, last row implicit 0 0 0 1)
+};
+
+struct ProjInfo {
+  int nu, nv, nviews;
+  long long rs, vs;   // element strides
+};
+
+// ------------------------------------------------------------ launchers
+// All launchers are asynchronous on `stream` and return cudaGetLastError().
+
+cudaError_t launch_compose(const double* P, const double* theta, const double* view_weight,
+                           const float* view_scale, int V, int fdk, double sid,
+                           const VolInfo& vi, ViewGeom* geom, double* Phat, cudaStream_t s);
+
+cudaError_t launch_forward(const void* proj, int dtype, const ProjInfo& pi, const ViewGeom* geom,
+                           const VolInfo& vi, int fdk, float* vol, cudaStream_t s);
+
+cudaError_t launch_grad_images(const void* proj, int dtype, const ProjInfo& pi, float2* grad,
+                               cudaStream_t s);
+
+cudaError_t launch_vjp_motion(const float* dvol, const void* proj, int dtype, const ProjInfo& pi,
+                              const float2* grad, const ViewGeom* geom, const VolInfo& vi,
+                              int fdk, int exact, float* partials, cudaStream_t s);
+
+cudaError_t launch_reduce_chain(const float* partials, int ntiles, const VolInfo& vi,
+                                const double* P, const double* theta, int V, double* dL_dPhat,
+                                double* dL_dtheta, cudaStream_t s);
+
+cudaError_t launch_vjp_proj(const float* dvol, const ProjInfo& pi, const ViewGeom* geom,
+                            const VolInfo& vi, int fdk, float* dproj, cudaStream_t s);
+
+cudaError_t launch_sharpness(const float* vol, int nx, int ny, int nz, double* block_sums,
+                             int max_blocks, double* loss, float* grad, cudaStream_t s);
+
+cudaError_t launch_gd(int V, double* theta, const double* grad, double s0, double t, int n,
+                      int gauge, cudaStream_t s);
+
+cudaError_t launch_adam(int V, double* theta, const double* grad, double* m1, double* m2,
+                        double lr, double b1, double b2, double eps, int n, int gauge,
+                        cudaStream_t s);
+
+int sharpness_blocks(long long nvox);
+
+}  // namespace bpk

@@ -1,0 +1,47 @@
+"""Seeded test cases shared by the oracle and GPU tests: every input comes
+from the workload generator (or plain numpy seeds), never from the CUDA path.
+The oracle side composes the moved geometry for the simulation."""
+from __future__ import annotations
+
+import functools
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2401_09283_gb300 import workloads as W
+
+
+@functools.lru_cache(maxsize=None)
+def scan_case(name: str, views=None, device="cpu"):
+    """(cfg, P, theta*, proj float32 numpy, delta float32 numpy) for a config;
+    `views` is an optional tuple of view indices to simulate."""
+    cfg = W.CONFIGS[name]
+    P = W.projection_matrices(cfg)
+    th = W.motion_curves(cfg)
+    Pm = oracle.compose(P, th)
+    sel = None if views is None else list(views)
+    sc = W.make_scan(cfg, moved_P=Pm, views=sel, device=device)
+    proj = sc.proj.cpu().numpy().astype(np.float32)
+    delta = W.upstream_gradient(cfg)
+    return cfg, P, th, proj, delta
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def random_case(seed, shape=(19, 21, 37), views=7, nu=40, nv=30, pitch=3.0, spacing=2.0,
+                motion_scale=1.0):
+    """A small ragged case: odd volume sizes, few views, random data."""
+    rng = np.random.default_rng(seed)
+    cfg = W.ScanConfig("rand%d" % seed, 0, spacing, views, 200.0, 750.0, 1200.0, nu, nv, pitch,
+                       0, 0, 0.0, 4, 2.0, 1.5, seed, seed)
+    P = W.projection_matrices(cfg)
+    th = rng.uniform(-1, 1, (views, 6)) * np.array([2, 2, 2, 0.02, 0.02, 0.02]) * motion_scale
+    proj = rng.standard_normal((views, nv, nu)).astype(np.float32)
+    delta = rng.standard_normal(shape).astype(np.float32)
+    origin = tuple(-(n - 1) / 2.0 * spacing for n in shape[::-1])
+    return cfg, P, th, proj, delta, origin
