@@ -100,6 +100,18 @@ const char* bp_last_error(const bp_ctx* ctx);
 /* Bytes of device workspace currently held by the context. */
 long long bp_ctx_workspace_bytes(const bp_ctx* ctx);
 
+/* Kernel accounting.  bp_ctx_launch_count: number of kernels the context
+ * has launched since it was created.  bp_ctx_set_timing(ctx, 1) resets the
+ * per-kernel totals and brackets every later launch with a pair of CUDA
+ * events on the launching stream; bp_ctx_timing() then waits for the
+ * recorded events and returns the summed device time (ms) and the number of
+ * launches of one kernel: "compose", "forward", "grad_images",
+ * "vjp_motion", "reduce_chain", "vjp_proj", "sharpness" or "optimizer".
+ * The paper has no counterpart; this is instrumentation for benchmarks. */
+long long bp_ctx_launch_count(const bp_ctx* ctx);
+int bp_ctx_set_timing(bp_ctx* ctx, int enable);
+int bp_ctx_timing(bp_ctx* ctx, const char* kernel, double* total_ms, long long* launches);
+
 /* Eq. 1 for every view: Phat[j] = P[j] T(motion[j]) (float64, [V][12]).
  * motion may be NULL (identity; Phat is then P bit for bit). */
 int bp_compose(bp_ctx* ctx, int nviews, const double* P, const double* motion, double* Phat,

@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "bp_gb300.h"
 #include "bp_internal.cuh"
@@ -16,9 +17,28 @@ struct Buf {
 
 }  // namespace
 
+namespace {
+enum KernelId {
+  K_COMPOSE, K_FORWARD, K_GRAD, K_VJP_MOTION, K_REDUCE, K_VJP_PROJ, K_SHARPNESS, K_OPT, K_COUNT
+};
+const char* const kKernelNames[K_COUNT] = {"compose", "forward", "grad_images", "vjp_motion",
+                                           "reduce_chain", "vjp_proj", "sharpness", "optimizer"};
+struct Pending {
+  int id;
+  cudaEvent_t a, b;
+};
+}  // namespace
+
 struct bp_ctx {
   int device = 0;
   std::string err;
+  // kernel accounting: launch counter (always) and optional event timing
+  long long launches = 0;
+  bool timing = false;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> spare;
+  double total_ms[K_COUNT] = {};
+  long long count[K_COUNT] = {};
   // workspace
   Buf geom, grad, partials, shblk;
   // staging of host arguments
@@ -59,6 +79,53 @@ int cuda_fail(bp_ctx* c, cudaError_t e, const char* where) {
     cudaError_t e_ = (expr);                         \
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
   } while (0)
+
+cudaEvent_t take_event(bp_ctx* c) {
+  if (!c->spare.empty()) {
+    cudaEvent_t e = c->spare.back();
+    c->spare.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Fold finished event pairs into the per-kernel totals (synchronises them).
+void resolve_timing(bp_ctx* c) {
+  for (const Pending& p : c->pending) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->total_ms[p.id] += ms;
+      c->count[p.id] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->spare.push_back(p.a);
+    c->spare.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
+// Launch nk kernels through f(); with timing on, bracket them by events.
+template <class F>
+cudaError_t timed(bp_ctx* c, int id, int nk, cudaStream_t s, F f) {
+  c->launches += nk;
+  if (!c->timing) return f();
+  cudaEvent_t a = take_event(c), b = take_event(c);
+  if (!a || !b) return f();
+  cudaEventRecord(a, s);
+  cudaError_t e = f();
+  cudaEventRecord(b, s);
+  c->pending.push_back({id, a, b});
+  if (c->pending.size() > 4096) resolve_timing(c);
+  return e;
+}
+
+#define TL(id, nk, expr) timed(ctx, id, nk, s, [&]() { return (expr); })
 
 // Grow a workspace buffer (contents are not preserved).
 cudaError_t ensure(Buf& b, size_t bytes) {
@@ -202,8 +269,8 @@ int prepare_views(bp_ctx* ctx, const bp_proj_desc* pd, const double* P, const do
   CK(stage_in(ctx->s_scale, pd->view_scale, sizeof(float) * V, s, &q), "copy view_scale");
   const float* dsc = (const float*)q;
   CK(ensure(ctx->geom, sizeof(ViewGeom) * (size_t)V), "alloc view table");
-  CK(bpk::launch_compose(*dP, *dmotion, dvw, dsc, V, weight == BP_WEIGHT_FDK, pd->sid, vi,
-                         (ViewGeom*)ctx->geom.p, nullptr, s),
+  CK(TL(K_COMPOSE, 1, bpk::launch_compose(*dP, *dmotion, dvw, dsc, V, weight == BP_WEIGHT_FDK,
+                                          pd->sid, vi, (ViewGeom*)ctx->geom.p, nullptr, s)),
      "compose");
   return BP_OK;
 }
@@ -243,6 +310,8 @@ void bp_ctx_destroy(bp_ctx* ctx) {
                  &ctx->s_theta, &ctx->s_grad, &ctx->s_m1,       &ctx->s_m2,       &ctx->s_loss};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
+  resolve_timing(ctx);
+  for (cudaEvent_t e : ctx->spare) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -258,6 +327,33 @@ long long bp_ctx_workspace_bytes(const bp_ctx* ctx) {
   for (const Buf* b : bufs) t += (long long)b->n;
   return t;
 }
+
+int bp_ctx_set_timing(bp_ctx* ctx, int enable) {
+  if (!ctx) return BP_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  resolve_timing(ctx);
+  for (int k = 0; k < K_COUNT; ++k) {
+    ctx->total_ms[k] = 0.0;
+    ctx->count[k] = 0;
+  }
+  ctx->timing = enable != 0;
+  return BP_OK;
+}
+
+int bp_ctx_timing(bp_ctx* ctx, const char* kernel, double* total_ms, long long* launches) {
+  if (!ctx || !kernel) return BP_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  resolve_timing(ctx);
+  for (int k = 0; k < K_COUNT; ++k)
+    if (std::strcmp(kernel, kKernelNames[k]) == 0) {
+      if (total_ms) *total_ms = ctx->total_ms[k];
+      if (launches) *launches = ctx->count[k];
+      return BP_OK;
+    }
+  return fail(ctx, BP_ERR_INVALID_ARG, std::string("unknown kernel name ") + kernel);
+}
+
+long long bp_ctx_launch_count(const bp_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 int bp_compose(bp_ctx* ctx, int nviews, const double* P, const double* motion, double* Phat,
                void* stream) {
@@ -277,7 +373,8 @@ int bp_compose(bp_ctx* ctx, int nviews, const double* P, const double* motion, d
   bool host;
   CK(stage_out(ctx->s_out_P, Phat, sizeof(double) * 12 * nviews, &o, &host), "alloc Phat");
   VolInfo vi{};
-  CK(bpk::launch_compose(dP, dm, nullptr, nullptr, nviews, 0, 0.0, vi, nullptr, (double*)o, s),
+  CK(TL(K_COMPOSE, 1, bpk::launch_compose(dP, dm, nullptr, nullptr, nviews, 0, 0.0, vi, nullptr,
+                                          (double*)o, s)),
      "compose");
   if (host) {
     CK(cudaMemcpyAsync(Phat, o, sizeof(double) * 12 * nviews, cudaMemcpyDeviceToHost, s),
@@ -317,8 +414,9 @@ int bp_forward(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, const d
     const double *dP, *dm;
     st = prepare_views(ctx, pdesc, P, motion, view_weight, weight, vi, s, &dP, &dm);
     if (st) return st;
-    CK(bpk::launch_forward(dproj, pdesc->dtype, make_projinfo(pdesc), (const ViewGeom*)ctx->geom.p,
-                           vi, weight == BP_WEIGHT_FDK, (float*)dvol, s),
+    CK(TL(K_FORWARD, 1, bpk::launch_forward(dproj, pdesc->dtype, make_projinfo(pdesc),
+                                          (const ViewGeom*)ctx->geom.p, vi,
+                                          weight == BP_WEIGHT_FDK, (float*)dvol, s)),
        "forward kernel");
   }
   if (host_vol) {
@@ -372,18 +470,20 @@ int bp_vjp(bp_ctx* ctx, const float* dL_dvol, const void* proj, const bp_proj_de
     const float2* grad = nullptr;
     if (deriv == BP_DERIV_CENTRAL) {
       CK(ensure(ctx->grad, sizeof(float2) * (size_t)V * pdesc->nv * pdesc->nu), "alloc grad");
-      CK(bpk::launch_grad_images(dproj, pdesc->dtype, pi, (float2*)ctx->grad.p, s), "grad images");
+      CK(TL(K_GRAD, 1, bpk::launch_grad_images(dproj, pdesc->dtype, pi, (float2*)ctx->grad.p, s)),
+         "grad images");
       grad = (const float2*)ctx->grad.p;
     }
     if (nvox > 0) {
       CK(ensure(ctx->partials, sizeof(float) * bpk::PSLOTS * (size_t)V * ntiles), "alloc partials");
-      CK(bpk::launch_vjp_motion(ddvol, dproj, pdesc->dtype, pi, grad, (const ViewGeom*)ctx->geom.p,
-                                vi, weight == BP_WEIGHT_FDK, deriv == BP_DERIV_BILINEAR_EXACT,
-                                (float*)ctx->partials.p, s),
+      CK(TL(K_VJP_MOTION, 1,
+            bpk::launch_vjp_motion(ddvol, dproj, pdesc->dtype, pi, grad,
+                                   (const ViewGeom*)ctx->geom.p, vi, weight == BP_WEIGHT_FDK,
+                                   deriv == BP_DERIV_BILINEAR_EXACT, (float*)ctx->partials.p, s)),
          "vjp kernel");
     }
-    CK(bpk::launch_reduce_chain((const float*)ctx->partials.p, nvox > 0 ? ntiles : 0, vi, dP, dm,
-                                V, (double*)oP, (double*)om, s),
+    CK(TL(K_REDUCE, 1, bpk::launch_reduce_chain((const float*)ctx->partials.p, nvox > 0 ? ntiles : 0,
+                                              vi, dP, dm, V, (double*)oP, (double*)om, s)),
        "reduce kernel");
   }
   if (dL_dproj) {
@@ -392,8 +492,8 @@ int bp_vjp(bp_ctx* ctx, const float* dL_dvol, const void* proj, const bp_proj_de
       ProjInfo po = pi;
       po.rs = pdesc->nu;
       po.vs = (long long)pdesc->nu * pdesc->nv;
-      CK(bpk::launch_vjp_proj(ddvol, po, (const ViewGeom*)ctx->geom.p, vi,
-                              weight == BP_WEIGHT_FDK, (float*)oD, s),
+      CK(TL(K_VJP_PROJ, 1, bpk::launch_vjp_proj(ddvol, po, (const ViewGeom*)ctx->geom.p, vi,
+                                                weight == BP_WEIGHT_FDK, (float*)oD, s)),
          "proj vjp kernel");
     }
   }
@@ -431,8 +531,9 @@ int bp_sharpness(bp_ctx* ctx, const float* vol, const bp_vol_desc* vdesc, double
   CK(stage_out(ctx->s_dvol, dL_dvol, sizeof(float) * nvox, &og, &hg), "alloc grad");
   const int nb = bpk::sharpness_blocks(nvox);
   CK(ensure(ctx->shblk, sizeof(double) * nb), "alloc block sums");
-  CK(bpk::launch_sharpness((const float*)q, vdesc->nx, vdesc->ny, vdesc->nz, (double*)ctx->shblk.p,
-                           nb, (double*)ol, (float*)og, s),
+  CK(TL(K_SHARPNESS, 2, bpk::launch_sharpness((const float*)q, vdesc->nx, vdesc->ny, vdesc->nz,
+                                              (double*)ctx->shblk.p, nb, (double*)ol,
+                                              (float*)og, s)),
      "sharpness kernel");
   if (hl) CK(cudaMemcpyAsync(loss, ol, sizeof(double), cudaMemcpyDeviceToHost, s), "copy loss");
   if (hg) CK(cudaMemcpyAsync(dL_dvol, og, sizeof(float) * nvox, cudaMemcpyDeviceToHost, s), "copy grad");
@@ -494,7 +595,7 @@ int bp_gd_step(bp_ctx* ctx, int nviews, double* theta, const double* grad, doubl
   cudaStream_t s = (cudaStream_t)stream;
   return opt_step(ctx, nviews, theta, grad, nullptr, nullptr, s,
                   [&](double* th, const double* gr, double*, double*) {
-                    return bpk::launch_gd(nviews, th, gr, s0, t, n, gauge, s);
+                    return TL(K_OPT, 1, bpk::launch_gd(nviews, th, gr, s0, t, n, gauge, s));
                   });
 }
 
@@ -510,8 +611,8 @@ int bp_adam_step(bp_ctx* ctx, int nviews, double* theta, const double* grad, dou
   cudaStream_t s = (cudaStream_t)stream;
   return opt_step(ctx, nviews, theta, grad, m1, m2, s,
                   [&](double* th, const double* gr, double* a, double* b) {
-                    return bpk::launch_adam(nviews, th, gr, a, b, lr, beta1, beta2, eps, n, gauge,
-                                            s);
+                    return TL(K_OPT, 1, bpk::launch_adam(nviews, th, gr, a, b, lr, beta1, beta2, eps, n,
+                                                         gauge, s));
                   });
 }
 

@@ -128,8 +128,12 @@ __device__ __forceinline__ Sample locate(float u, float v, float w, const TileVi
   s.rwi = rcp_approx(w);
   float x = u * s.rwi, y = v * s.rwi;
   if (EDGE) {
-    x = fminf(fmaxf(x, -1.0f - (float)t.au), (float)(nu - t.au));
-    y = fminf(fmaxf(y, -1.0f - (float)t.av), (float)(nv - t.av));
+    // Clamp far-off coordinates into (-2, -1) or (n, n+1): all four taps are
+    // then outside the detector, so value and derivatives are 0 there (a
+    // clamp to exactly -1 would sit on the kink of the zero-padded
+    // interpolant, where the exact derivative is d[0], not 0).
+    x = fminf(fmaxf(x, -1.5f - (float)t.au), (float)nu + 0.5f - (float)t.au);
+    y = fminf(fmaxf(y, -1.5f - (float)t.av), (float)nv + 0.5f - (float)t.av);
   }
   float rx = __fadd_rd(x, MAGIC), ry = __fadd_rd(y, MAGIC);
   s.tu = x - (rx - MAGIC);

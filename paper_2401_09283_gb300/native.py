@@ -48,6 +48,7 @@ _lock = threading.Lock()
 _ctx = {}
 
 EXPORTS = ["bp_ctx_create", "bp_ctx_destroy", "bp_last_error", "bp_ctx_workspace_bytes",
+           "bp_ctx_launch_count", "bp_ctx_set_timing", "bp_ctx_timing",
            "bp_compose", "bp_forward", "bp_vjp", "bp_sharpness", "bp_gd_step", "bp_adam_step"]
 
 
@@ -71,6 +72,11 @@ def lib():
                 L.bp_last_error.restype = ctypes.c_char_p
                 L.bp_ctx_workspace_bytes.argtypes = [vp]
                 L.bp_ctx_workspace_bytes.restype = c_ll
+                L.bp_ctx_launch_count.argtypes = [vp]
+                L.bp_ctx_launch_count.restype = c_ll
+                L.bp_ctx_set_timing.argtypes = [vp, c_int]
+                L.bp_ctx_timing.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(c_double),
+                                            ctypes.POINTER(c_ll)]
                 L.bp_compose.argtypes = [vp, c_int, vp, vp, vp, vp]
                 L.bp_forward.argtypes = [vp, vp, ctypes.POINTER(ProjDesc), vp, vp, vp, c_int,
                                          ctypes.POINTER(VolDesc), vp, vp]
@@ -157,3 +163,29 @@ def proj_desc(proj, sid=0.0, view_scale=None):
     V, nv, nu = proj.shape
     return ProjDesc(int(nu), int(nv), int(V), _DT[dt], int(nu), int(nu) * int(nv),
                     ptr(view_scale), float(sid))
+
+
+KERNELS = ("compose", "forward", "grad_images", "vjp_motion", "reduce_chain", "vjp_proj",
+           "sharpness", "optimizer")
+
+
+def set_timing(enable=True, device=None):
+    ctx = context(device)
+    check("bp_ctx_set_timing", lib().bp_ctx_set_timing(ctx, int(bool(enable))), ctx)
+
+
+def kernel_times(device=None):
+    """{kernel: (total device ms, launches)} since set_timing(True)."""
+    ctx = context(device)
+    out = {}
+    for k in KERNELS:
+        ms = c_double()
+        n = c_ll()
+        check("bp_ctx_timing", lib().bp_ctx_timing(ctx, k.encode(), ctypes.byref(ms),
+                                                   ctypes.byref(n)), ctx)
+        out[k] = (ms.value, n.value)
+    return out
+
+
+def launch_count(device=None):
+    return int(lib().bp_ctx_launch_count(context(device)))
