@@ -157,6 +157,29 @@ int bp_vjp(bp_ctx* ctx, const float* dL_dvol, const void* proj, const bp_proj_de
 int bp_sharpness(bp_ctx* ctx, const float* vol, const bp_vol_desc* vdesc, double* loss,
                  float* dL_dvol, void* stream);
 
+/* Allocation-free sharpness loss.  The paper has no counterpart: this is for
+ * callers that cannot allocate device memory during the call -- code being
+ * recorded into a CUDA graph (an allocation would break the stream capture),
+ * hosts that give all device memory to their own pool at start-up, and
+ * real-time loops that must not wait on the allocator.  It computes exactly
+ * what bp_sharpness computes, needs no context, allocates nothing (no
+ * cudaMalloc/cudaFree, no allocating library routine) and keeps its per-chunk
+ * FP64 partial sums in a fixed array inside the library: 256 KiB on every GPU
+ * that loads the library, held until the process exits.
+ *   vol, dL_dvol, loss  device memory of the current device (host pointers
+ *                       are rejected with BP_ERR_INVALID_ARG); dL_dvol may
+ *                       be NULL;
+ *   limit               at most 512^3 = 134217728 voxels; larger volumes
+ *                       return BP_ERR_UNSUPPORTED.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Calls
+ * share the array: calls whose kernels may overlap on the GPU (other streams,
+ * other host threads) race and give wrong results.  Every call overwrites
+ * all partials it reads, so no state carries over.  Asynchronous on
+ * `stream`.  Errors are reported by the return code only. */
+int bp_sharpness_noalloc(const float* vol, const bp_vol_desc* vdesc, double* loss,
+                         float* dL_dvol, void* stream);
+
 /* Optimiser steps on theta float64 [V][6] in place (device or host).
  * Eq. 6: theta -= s0 * t^n * grad.  Adam: standard bias-corrected Adam with
  * iteration counter n >= 1 and moments m1, m2 ([V][6], caller-owned, start

@@ -49,7 +49,8 @@ _ctx = {}
 
 EXPORTS = ["bp_ctx_create", "bp_ctx_destroy", "bp_last_error", "bp_ctx_workspace_bytes",
            "bp_ctx_launch_count", "bp_ctx_set_timing", "bp_ctx_timing",
-           "bp_compose", "bp_forward", "bp_vjp", "bp_sharpness", "bp_gd_step", "bp_adam_step"]
+           "bp_compose", "bp_forward", "bp_vjp", "bp_sharpness", "bp_sharpness_noalloc",
+           "bp_gd_step", "bp_adam_step"]
 
 
 def lib():
@@ -83,6 +84,7 @@ def lib():
                 L.bp_vjp.argtypes = [vp, vp, vp, ctypes.POINTER(ProjDesc), vp, vp, vp, c_int,
                                      c_int, ctypes.POINTER(VolDesc), vp, vp, vp, vp]
                 L.bp_sharpness.argtypes = [vp, vp, ctypes.POINTER(VolDesc), vp, vp, vp]
+                L.bp_sharpness_noalloc.argtypes = [vp, ctypes.POINTER(VolDesc), vp, vp, vp]
                 L.bp_gd_step.argtypes = [vp, c_int, vp, vp, c_double, c_double, c_int, c_int, vp]
                 L.bp_adam_step.argtypes = [vp, c_int, vp, vp, vp, vp, c_double, c_double,
                                            c_double, c_double, c_int, c_int, vp]
