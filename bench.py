@@ -43,6 +43,7 @@ PASS_COST = {
     "forward": {"fp32": 16, "samples": 4},      # FDK weighting
     "vjp_motion": {"fp32": 38, "samples": 12},  # CENTRAL g_u, g_v + FDK value
     "vjp_proj": {"fp32": 12, "samples": 4},
+    "vjp_fused": {"fp32": 50, "samples": 16},   # motion and data VJP in one pass
 }
 
 

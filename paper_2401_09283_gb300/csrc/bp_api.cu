@@ -19,10 +19,12 @@ struct Buf {
 
 namespace {
 enum KernelId {
-  K_COMPOSE, K_FORWARD, K_GRAD, K_VJP_MOTION, K_REDUCE, K_VJP_PROJ, K_SHARPNESS, K_OPT, K_COUNT
+  K_COMPOSE, K_FORWARD, K_GRAD, K_VJP_MOTION, K_REDUCE, K_VJP_PROJ, K_VJP_FUSED, K_SHARPNESS,
+  K_OPT, K_COUNT
 };
-const char* const kKernelNames[K_COUNT] = {"compose", "forward", "grad_images", "vjp_motion",
-                                           "reduce_chain", "vjp_proj", "sharpness", "optimizer"};
+const char* const kKernelNames[K_COUNT] = {"compose",  "forward",   "grad_images",
+                                           "vjp_motion", "reduce_chain", "vjp_proj",
+                                           "vjp_fused",  "sharpness", "optimizer"};
 struct Pending {
   int id;
   cudaEvent_t a, b;
@@ -466,6 +468,9 @@ int bp_vjp(bp_ctx* ctx, const float* dL_dvol, const void* proj, const bp_proj_de
   CK(stage_out(ctx->s_out_P, dL_dPhat, sizeof(double) * 12 * V, &oP, &hP), "alloc out");
   const size_t dproj_bytes = sizeof(float) * (size_t)V * pdesc->nv * pdesc->nu;
   CK(stage_out(ctx->s_out_proj, dL_dproj, dproj_bytes, &oD, &hD), "alloc out");
+  // the data VJP is fused into the motion-VJP kernel when both are wanted
+  const bool fuse = want_geo && dL_dproj && nvox > 0;
+  if (dL_dproj) CK(cudaMemsetAsync(oD, 0, dproj_bytes, s), "zero dL_dproj");
   if (want_geo) {
     const float2* grad = nullptr;
     if (deriv == BP_DERIV_CENTRAL) {
@@ -476,26 +481,24 @@ int bp_vjp(bp_ctx* ctx, const float* dL_dvol, const void* proj, const bp_proj_de
     }
     if (nvox > 0) {
       CK(ensure(ctx->partials, sizeof(float) * bpk::PSLOTS * (size_t)V * ntiles), "alloc partials");
-      CK(TL(K_VJP_MOTION, 1,
+      CK(TL(fuse ? K_VJP_FUSED : K_VJP_MOTION, 1,
             bpk::launch_vjp_motion(ddvol, dproj, pdesc->dtype, pi, grad,
                                    (const ViewGeom*)ctx->geom.p, vi, weight == BP_WEIGHT_FDK,
-                                   deriv == BP_DERIV_BILINEAR_EXACT, (float*)ctx->partials.p, s)),
+                                   deriv == BP_DERIV_BILINEAR_EXACT, (float*)ctx->partials.p,
+                                   fuse ? (float*)oD : nullptr, s)),
          "vjp kernel");
     }
     CK(TL(K_REDUCE, 1, bpk::launch_reduce_chain((const float*)ctx->partials.p, nvox > 0 ? ntiles : 0,
                                               vi, dP, dm, V, (double*)oP, (double*)om, s)),
        "reduce kernel");
   }
-  if (dL_dproj) {
-    CK(cudaMemsetAsync(oD, 0, dproj_bytes, s), "zero dL_dproj");
-    if (nvox > 0) {
-      ProjInfo po = pi;
-      po.rs = pdesc->nu;
-      po.vs = (long long)pdesc->nu * pdesc->nv;
-      CK(TL(K_VJP_PROJ, 1, bpk::launch_vjp_proj(ddvol, po, (const ViewGeom*)ctx->geom.p, vi,
-                                                weight == BP_WEIGHT_FDK, (float*)oD, s)),
-         "proj vjp kernel");
-    }
+  if (dL_dproj && !fuse && nvox > 0) {
+    ProjInfo po = pi;
+    po.rs = pdesc->nu;
+    po.vs = (long long)pdesc->nu * pdesc->nv;
+    CK(TL(K_VJP_PROJ, 1, bpk::launch_vjp_proj(ddvol, po, (const ViewGeom*)ctx->geom.p, vi,
+                                              weight == BP_WEIGHT_FDK, (float*)oD, s)),
+       "proj vjp kernel");
   }
   if (hm) CK(cudaMemcpyAsync(dL_dmotion, om, sizeof(double) * 6 * V, cudaMemcpyDeviceToHost, s), "copy out");
   if (hP) CK(cudaMemcpyAsync(dL_dPhat, oP, sizeof(double) * 12 * V, cudaMemcpyDeviceToHost, s), "copy out");

@@ -42,8 +42,11 @@ struct TileView {
   float rv[3];
   float rw[3];
   int au, av;         // anchor pixel
-  float wgt;          // wgt * scale (FP32)
+  float wgt;          // wgt * scale (FP32): weight of a stored sample
+  float wgtd;         // wgt alone: weight of a dequantised sample (data VJP)
   int mode;           // MODE_*
+  int fu0, fv0;       // detector footprint of the tile (first pixel), clipped
+  int fw, fh;         // footprint size in pixels (0 when unbounded)
 };
 
 enum { MODE_SKIP = 0, MODE_INTERIOR = 1, MODE_EDGE = 2 };
@@ -74,9 +77,11 @@ cudaError_t launch_forward(const void* proj, int dtype, const ProjInfo& pi, cons
 cudaError_t launch_grad_images(const void* proj, int dtype, const ProjInfo& pi, float2* grad,
                                cudaStream_t s);
 
+// dproj != NULL fuses the data VJP (same samples, contiguous [V][nv][nu]
+// output zeroed by the caller) into the motion-VJP kernel.
 cudaError_t launch_vjp_motion(const float* dvol, const void* proj, int dtype, const ProjInfo& pi,
                               const float2* grad, const ViewGeom* geom, const VolInfo& vi,
-                              int fdk, int exact, float* partials, cudaStream_t s);
+                              int fdk, int exact, float* partials, float* dproj, cudaStream_t s);
 
 cudaError_t launch_reduce_chain(const float* partials, int ntiles, const VolInfo& vi,
                                 const double* P, const double* theta, int V, double* dL_dPhat,

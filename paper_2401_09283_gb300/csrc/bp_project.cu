@@ -16,6 +16,16 @@
 
 namespace bpk {
 
+// CTAs per SM the register budget is sized for (256 threads each).
+#ifndef BP_FWD_MINB
+#define BP_FWD_MINB 3
+#endif
+#ifndef BP_VJP_MINB
+#define BP_VJP_MINB 3
+#endif
+constexpr int FWD_MINB = BP_FWD_MINB;
+constexpr int VJP_MINB = BP_VJP_MINB;
+
 constexpr float MAGIC = 12582912.0f;   // 1.5 * 2^23
 constexpr int MAGIC_BITS = 0x4B400000;
 
@@ -42,72 +52,129 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 // ------------------------------------------------------------ tile set-up
 
-// FP64 set-up of one (tile, view) record.  qc: tile centre in the index
-// frame; half: half-extent of the box of voxel centres.
-__device__ void setup_tile_view(TileView& t, const ViewGeom& g, const double qc[3],
-                                const double half[3], int nu, int nv, bool with_scale) {
+struct TileIdx {
+  int tx, ty, tz, lx, ly;
+  float dx, dy;
+  double qc[3];
+  float half[3];
+};
+
+template <int ZB>
+__device__ __forceinline__ TileIdx tile_index(const VolInfo& vi) {
+  TileIdx ti;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  ti.lx = (warp & 1) * 8 + (lane & 7);
+  ti.ly = (warp >> 1) * 4 + (lane >> 3);
+  const int tile = blockIdx.x;
+  ti.tx = tile % vi.tiles_x;
+  ti.ty = (tile / vi.tiles_x) % vi.tiles_y;
+  ti.tz = tile / (vi.tiles_x * vi.tiles_y);
+  ti.dx = ti.lx - 0.5f * (TX - 1);
+  ti.dy = ti.ly - 0.5f * (TY - 1);
+  ti.qc[0] = ti.tx * TX + 0.5 * (TX - 1) - vi.cx;
+  ti.qc[1] = ti.ty * TY + 0.5 * (TY - 1) - vi.cy;
+  ti.qc[2] = ti.tz * ZB + 0.5 * (ZB - 1) - vi.cz;
+  ti.half[0] = 0.5f * (TX - 1);
+  ti.half[1] = 0.5f * (TY - 1);
+  ti.half[2] = 0.5f * (ZB - 1);
+  return ti;
+}
+
+// Cooperative set-up of the records of views j0 .. j0+nb-1 (nb <= 32) for
+// this CTA's box; every thread of the CTA must call it.  Eight lanes serve
+// one view; lane c evaluates box corner c.  FP64 is used only where the
+// precision matters -- the projection (uc, vc, wc) of the tile centre and
+// the anchored values U0 = uc - au wc, V0 = vc - av wc; the anchor pixel
+// itself only has to be near the projection and comes from FP32.  The
+// corners are evaluated in FP32 in the anchored frame (errors ~1e-5 px,
+// far below the 0.01 px classification margin): u/w and v/w are
+// linear-fractional in the voxel position, so over a box with w > 0 their
+// extremes are at the corners, and the box is
+//   SKIP      every sample is 0 (projection at or beyond -1 / n),
+//   INTERIOR  every tap (floor and floor+1) lies on the detector,
+//   EDGE      otherwise (clamped coordinates, checked taps).
+// The footprint is the clipped pixel rectangle that the box's taps can
+// touch (unbounded, fw = 0, when some corner has w <= 0).
+__device__ void setup_batch(TileView* tvs, const ViewGeom* __restrict__ geom, int j0, int nb,
+                            const TileIdx& ti, int nu, int nv, bool with_scale) {
+  const int b = threadIdx.x >> 3, c = threadIdx.x & 7;
+  const ViewGeom& g = geom[j0 + min(b, nb - 1)];
   const double* M = g.P;
-  double uc = fma(M[0], qc[0], fma(M[1], qc[1], fma(M[2], qc[2], M[3])));
-  double vc = fma(M[4], qc[0], fma(M[5], qc[1], fma(M[6], qc[2], M[7])));
-  double wc = fma(M[8], qc[0], fma(M[9], qc[1], fma(M[10], qc[2], M[11])));
+  const double uc = fma(M[0], ti.qc[0], fma(M[1], ti.qc[1], fma(M[2], ti.qc[2], M[3])));
+  const double vc = fma(M[4], ti.qc[0], fma(M[5], ti.qc[1], fma(M[6], ti.qc[2], M[7])));
+  const double wc = fma(M[8], ti.qc[0], fma(M[9], ti.qc[1], fma(M[10], ti.qc[2], M[11])));
   int au = 0, av = 0;
   if (wc > 0.0) {
-    double a = floor(uc / wc), b = floor(vc / wc);
-    a = fmin(fmax(a, -1048576.0), 1048576.0);
-    b = fmin(fmax(b, -1048576.0), 1048576.0);
+    const float wf = (float)wc;
+    const float a = fminf(fmaxf(floorf((float)uc / wf), -1048576.0f), 1048576.0f);
+    const float bq = fminf(fmaxf(floorf((float)vc / wf), -1048576.0f), 1048576.0f);
     au = (int)a;
-    av = (int)b;
+    av = (int)bq;
   }
-  double Ru[4], Rv[4], Rw[4];
-  for (int k = 0; k < 4; ++k) {
-    Ru[k] = M[k] - au * M[8 + k];
-    Rv[k] = M[4 + k] - av * M[8 + k];
-    Rw[k] = M[8 + k];
-  }
-  double U0 = fma(Ru[0], qc[0], fma(Ru[1], qc[1], fma(Ru[2], qc[2], Ru[3])));
-  double V0 = fma(Rv[0], qc[0], fma(Rv[1], qc[1], fma(Rv[2], qc[2], Rv[3])));
-  double W0 = wc;
-  t.U0 = (float)U0;
-  t.V0 = (float)V0;
-  t.W0 = (float)W0;
+  TileView t;
+  t.U0 = (float)fma(-(double)au, wc, uc);
+  t.V0 = (float)fma(-(double)av, wc, vc);
+  t.W0 = (float)wc;
+  const float fau = (float)au, fav = (float)av;
+#pragma unroll
   for (int k = 0; k < 3; ++k) {
-    t.ru[k] = (float)Ru[k];
-    t.rv[k] = (float)Rv[k];
-    t.rw[k] = (float)Rw[k];
+    const float m2 = (float)M[8 + k];
+    t.ru[k] = fmaf(-fau, m2, (float)M[k]);
+    t.rv[k] = fmaf(-fav, m2, (float)M[4 + k]);
+    t.rw[k] = m2;
   }
   t.au = au;
   t.av = av;
   t.wgt = (float)(with_scale ? g.wgt * g.scale : g.wgt);
-  // classify the box by its 8 corners (u/w and v/w are linear-fractional, so
-  // their extremes over a box with w > 0 are at the corners)
-  int npos = 0;
-  double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
-  for (int c = 0; c < 8; ++c) {
-    double d0 = (c & 1) ? half[0] : -half[0];
-    double d1 = (c & 2) ? half[1] : -half[1];
-    double d2 = (c & 4) ? half[2] : -half[2];
-    double w = W0 + Rw[0] * d0 + Rw[1] * d1 + Rw[2] * d2;
-    if (!(w > 0.0)) continue;
-    ++npos;
-    double u = (U0 + Ru[0] * d0 + Ru[1] * d1 + Ru[2] * d2) / w + au;
-    double v = (V0 + Rv[0] * d0 + Rv[1] * d1 + Rv[2] * d2) / w + av;
-    umin = fmin(umin, u);
-    umax = fmax(umax, u);
-    vmin = fmin(vmin, v);
-    vmax = fmax(vmax, v);
+  t.wgtd = (float)g.wgt;
+  // this lane's corner
+  const float d0 = (c & 1) ? ti.half[0] : -ti.half[0];
+  const float d1 = (c & 2) ? ti.half[1] : -ti.half[1];
+  const float d2 = (c & 4) ? ti.half[2] : -ti.half[2];
+  const float w = fmaf(t.rw[2], d2, fmaf(t.rw[1], d1, fmaf(t.rw[0], d0, t.W0)));
+  const float u = fmaf(t.ru[2], d2, fmaf(t.ru[1], d1, fmaf(t.ru[0], d0, t.U0)));
+  const float v = fmaf(t.rv[2], d2, fmaf(t.rv[1], d1, fmaf(t.rv[0], d0, t.V0)));
+  const bool pos = w > 0.0f;
+  int npos = pos ? 1 : 0;
+  float xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY;
+  if (pos) {
+    xmin = xmax = u / w;
+    ymin = ymax = v / w;
   }
-  const double m = 0.01;  // >> the FP32 coordinate error of the inner loops
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    npos += __shfl_xor_sync(0xffffffffu, npos, o);
+    xmin = fminf(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
+    xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    ymin = fminf(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
+    ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+  }
+  if (c != 0 || b >= nb) return;
+  const float m = 0.01f;
+  // detector [0, n-1] in the anchored frame
+  const float ulo = -fau, uhi = (float)(nu - 1) - fau, vlo = -fav, vhi = (float)(nv - 1) - fav;
+  t.fu0 = t.fv0 = t.fw = t.fh = 0;
   if (npos == 0) {
     t.mode = MODE_SKIP;
   } else if (npos < 8) {
     t.mode = MODE_EDGE;
-  } else if (umax <= -1.0 - m || umin >= nu + m || vmax <= -1.0 - m || vmin >= nv + m) {
+  } else if (xmax <= ulo - 1.0f - m || xmin >= uhi + 1.0f + m || ymax <= vlo - 1.0f - m ||
+             ymin >= vhi + 1.0f + m) {
     t.mode = MODE_SKIP;
-  } else if (umin >= m && umax <= nu - 1 - m && vmin >= m && vmax <= nv - 1 - m) {
-    t.mode = MODE_INTERIOR;
   } else {
-    t.mode = MODE_EDGE;
+    t.mode = (xmin >= ulo + m && xmax <= uhi - m && ymin >= vlo + m && ymax <= vhi - m)
+                 ? MODE_INTERIOR
+                 : MODE_EDGE;
+    const int u0 = max((int)floorf(xmin - m) + au, 0), u1 = min((int)floorf(xmax + m) + 1 + au, nu - 1);
+    const int v0 = max((int)floorf(ymin - m) + av, 0), v1 = min((int)floorf(ymax + m) + 1 + av, nv - 1);
+    if (u1 >= u0 && v1 >= v0) {
+      t.fu0 = u0;
+      t.fv0 = v0;
+      t.fw = u1 - u0 + 1;
+      t.fh = v1 - v0 + 1;
+    }
   }
+  tvs[b] = t;
 }
 
 // Detector position of one voxel in the anchored frame.
@@ -173,39 +240,115 @@ __device__ __forceinline__ float bilerp(float tu, float tv, float d00, float d10
   return fmaf(tv, bot - top, top);
 }
 
-struct TileIdx {
-  int tx, ty, tz, lx, ly;
-  float dx, dy;
-  double qc[3], half[3];
+// ------------------------------------------------------ footprint staging
+
+// Each (tile, view) reads a small rectangle of one detector image (the tile
+// footprint from the set-up).  Voxels project ~2.6 px apart on the larger
+// detectors, so a warp's 32 taps of one load are scattered over 4-6 L1
+// lines; from shared memory the same taps are a single conflict-free
+// wavefront.  The footprint (plus an optional halo) is therefore copied to
+// shared memory with cp.async in 16-byte chunks, double-buffered across
+// views: the copy of view j+1 overlaps the arithmetic of view j.  Footprints
+// that do not fit the buffer, or are unbounded, read global memory instead.
+constexpr int STAGE_BYTES = 24576;  // per buffer; two buffers per CTA
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait1() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+// A staged rectangle: rows [v0, v0+h), columns [x0, x0 + cpr*CH), stored
+// with row pitch `pitch` elements.
+struct Stage {
+  int x0, v0, h, pitch, cpr;
+  bool on;
 };
 
-template <int ZB>
-__device__ __forceinline__ TileIdx tile_index(const VolInfo& vi) {
-  TileIdx ti;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  ti.lx = (warp & 1) * 8 + (lane & 7);
-  ti.ly = (warp >> 1) * 4 + (lane >> 3);
-  const int tile = blockIdx.x;
-  ti.tx = tile % vi.tiles_x;
-  ti.ty = (tile / vi.tiles_x) % vi.tiles_y;
-  ti.tz = tile / (vi.tiles_x * vi.tiles_y);
-  ti.dx = ti.lx - 0.5f * (TX - 1);
-  ti.dy = ti.ly - 0.5f * (TY - 1);
-  ti.qc[0] = ti.tx * TX + 0.5 * (TX - 1) - vi.cx;
-  ti.qc[1] = ti.ty * TY + 0.5 * (TY - 1) - vi.cy;
-  ti.qc[2] = ti.tz * ZB + 0.5 * (ZB - 1) - vi.cz;
-  ti.half[0] = 0.5 * (TX - 1);
-  ti.half[1] = 0.5 * (TY - 1);
-  ti.half[2] = 0.5 * (ZB - 1);
-  return ti;
+template <typename T>
+__device__ __forceinline__ Stage stage_plan(const TileView& t, int halo, int nu, int nv) {
+  constexpr int CH = 16 / (int)sizeof(T);
+  Stage st;
+  st.on = false;
+  st.x0 = st.v0 = st.h = st.pitch = st.cpr = 0;
+  if (t.mode == MODE_SKIP || t.fw <= 0) return st;
+  const int u0 = max(t.fu0 - halo, 0), u1 = min(t.fu0 + t.fw - 1 + halo, nu - 1);
+  const int v0 = max(t.fv0 - halo, 0), v1 = min(t.fv0 + t.fh - 1 + halo, nv - 1);
+  st.x0 = u0 & ~(CH - 1);
+  st.cpr = (u1 - st.x0) / CH + 1;
+  st.pitch = (st.cpr + 1) * CH;  // one spare chunk per row staggers the banks
+  st.v0 = v0;
+  st.h = v1 - v0 + 1;
+  st.on = st.cpr <= 32 && st.pitch * st.h * (int)sizeof(T) <= STAGE_BYTES;
+  return st;
+}
+
+// All threads: issue the copies of one staged rectangle (rows per warp,
+// chunks per lane, no divisions per chunk).
+template <typename T>
+__device__ __forceinline__ void stage_issue(T* buf, const T* img, long long rs, const Stage& st) {
+  constexpr int CH = 16 / (int)sizeof(T);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rpp = 32 / st.cpr;  // rows per warp pass
+  const int lr = lane / st.cpr, lc = lane - lr * st.cpr;
+  if (lr >= rpp) return;
+  for (int r = warp * rpp + lr; r < st.h; r += (NT / 32) * rpp)
+    cp_async16(buf + r * st.pitch + lc * CH, img + (long long)(st.v0 + r) * rs + st.x0 + lc * CH);
+}
+
+template <typename T>
+__device__ __forceinline__ float tof(T x);
+template <>
+__device__ __forceinline__ float tof<float>(float x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ float tof<__half>(__half x) {
+  return __half2float(x);
+}
+template <>
+__device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+
+// Four taps from a staged rectangle, zero outside the detector.
+template <bool EDGE, typename T>
+__device__ __forceinline__ void taps_smem(const T* buf, const Stage& st, int nu, int nv,
+                                          const Sample& s, float& d00, float& d10, float& d01,
+                                          float& d11) {
+  const int o = (s.iv - st.v0) * st.pitch + (s.iu - st.x0);
+  if (!EDGE) {
+    d00 = tof(buf[o]);
+    d10 = tof(buf[o + 1]);
+    d01 = tof(buf[o + st.pitch]);
+    d11 = tof(buf[o + st.pitch + 1]);
+  } else {
+    // off-detector taps may lie outside the staged rectangle: read a safe
+    // address and discard
+    const bool u0 = (unsigned)s.iu < (unsigned)nu, u1 = (unsigned)(s.iu + 1) < (unsigned)nu;
+    const bool v0 = (unsigned)s.iv < (unsigned)nv, v1 = (unsigned)(s.iv + 1) < (unsigned)nv;
+    const bool k00 = u0 && v0 && s.ok, k10 = u1 && v0 && s.ok;
+    const bool k01 = u0 && v1 && s.ok, k11 = u1 && v1 && s.ok;
+    const float a = tof(buf[k00 ? o : 0]), b = tof(buf[k10 ? o + 1 : 0]);
+    const float c = tof(buf[k01 ? o + st.pitch : 0]), d = tof(buf[k11 ? o + st.pitch + 1 : 0]);
+    d00 = k00 ? a : 0.0f;
+    d10 = k10 ? b : 0.0f;
+    d01 = k01 ? c : 0.0f;
+    d11 = k11 ? d : 0.0f;
+  }
 }
 
 // ------------------------------------------------------------------ forward
 
-template <int ZB, typename T, bool FDK, bool EDGE>
-__device__ __forceinline__ void forward_view(const T* img, long long rs, int nu, int nv,
-                                             const TileView& t, float dx, float dy,
-                                             float (&acc)[ZB]) {
+template <int ZB, typename T, bool FDK, bool EDGE, bool SMEM>
+__device__ __forceinline__ void forward_view(const T* img, const T* buf, const Stage& st,
+                                             long long rs, int nu, int nv, const TileView& t,
+                                             float dx, float dy, float (&acc)[ZB]) {
   float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
   float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
   float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
@@ -216,38 +359,78 @@ __device__ __forceinline__ void forward_view(const T* img, long long rs, int nu,
                             t, nu, nv);
     if (EDGE && !s.ok) continue;
     float d00, d10, d01, d11;
-    taps<EDGE>(img, rs, nu, nv, s, d00, d10, d01, d11);
+    if (SMEM)
+      taps_smem<EDGE>(buf, st, nu, nv, s, d00, d10, d01, d11);
+    else
+      taps<EDGE>(img, rs, nu, nv, s, d00, d10, d01, d11);
     float val = bilerp(s.tu, s.tv, d00, d10, d01, d11);
     float wv = FDK ? s.rwi * (s.rwi * t.wgt) : t.wgt;
     acc[k] = fmaf(val, wv, acc[k]);
   }
 }
 
-template <int ZB, typename T, bool FDK>
-__global__ void __launch_bounds__(NT, 2)
+// Views are processed in order; the records of batch k+1 are built at the
+// start of batch k (two record slots), so the footprint of view j+1 is
+// known, and its copy issued, while view j is computed.
+template <int ZB, typename T, bool FDK, bool STAGE>
+__global__ void __launch_bounds__(NT, FWD_MINB)
     forward_kernel(const T* __restrict__ proj, ProjInfo pi, const ViewGeom* __restrict__ geom,
                    VolInfo vi, float* __restrict__ vol) {
-  __shared__ TileView tvs[VB];
+  __shared__ TileView tvs[2][VB];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* bufs = reinterpret_cast<T*>(dyn_smem);
+  constexpr int CAP = STAGE_BYTES / (int)sizeof(T);
   const TileIdx ti = tile_index<ZB>(vi);
   float acc[ZB];
 #pragma unroll
   for (int k = 0; k < ZB; ++k) acc[k] = 0.0f;
-  for (int j0 = 0; j0 < pi.nviews; j0 += VB) {
-    const int nb = min(VB, pi.nviews - j0);
-    __syncthreads();
-    if (threadIdx.x < nb)
-      setup_tile_view(tvs[threadIdx.x], geom[j0 + threadIdx.x], ti.qc, ti.half, pi.nu, pi.nv,
-                      true);
-    __syncthreads();
-    for (int b = 0; b < nb; ++b) {
-      const TileView t = tvs[b];
-      if (t.mode == MODE_SKIP) continue;
-      const T* img = proj + (long long)(j0 + b) * pi.vs;
-      if (t.mode == MODE_INTERIOR)
-        forward_view<ZB, T, FDK, false>(img, pi.rs, pi.nu, pi.nv, t, ti.dx, ti.dy, acc);
-      else
-        forward_view<ZB, T, FDK, true>(img, pi.rs, pi.nu, pi.nv, t, ti.dx, ti.dy, acc);
+  const int V = pi.nviews;
+  const int nbatch = (V + VB - 1) / VB;
+  setup_batch(tvs[0], geom, 0, min(VB, V), ti, pi.nu, pi.nv, true);
+  if (nbatch > 1) setup_batch(tvs[1], geom, VB, min(VB, V - VB), ti, pi.nu, pi.nv, true);
+  __syncthreads();
+  Stage st_cur = STAGE ? stage_plan<T>(tvs[0][0], 0, pi.nu, pi.nv) : Stage{0, 0, 0, 0, 0, false};
+  if (STAGE && st_cur.on) stage_issue(bufs, proj, pi.rs, st_cur);
+  cp_async_commit();
+  for (int v = 0; v < V; ++v) {
+    const int k = v / VB, b = v - k * VB;
+    if (b == 0 && k >= 1 && k + 1 < nbatch) {
+      setup_batch(tvs[(k + 1) & 1], geom, (k + 1) * VB, min(VB, V - (k + 1) * VB), ti, pi.nu,
+                  pi.nv, true);
+      __syncthreads();
     }
+    const TileView t = tvs[k & 1][b];
+    Stage st_next = Stage{0, 0, 0, 0, 0, false};
+    if (STAGE && v + 1 < V) {
+      const int kn = (v + 1) / VB;
+      st_next = stage_plan<T>(tvs[kn & 1][v + 1 - kn * VB], 0, pi.nu, pi.nv);
+      if (st_next.on)
+        stage_issue(bufs + ((v + 1) & 1) * CAP, proj + (long long)(v + 1) * pi.vs, pi.rs, st_next);
+    }
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    if (t.mode != MODE_SKIP) {
+      const T* img = proj + (long long)v * pi.vs;
+      const T* buf = bufs + (v & 1) * CAP;
+      if (st_cur.on) {
+        if (t.mode == MODE_INTERIOR)
+          forward_view<ZB, T, FDK, false, true>(img, buf, st_cur, pi.rs, pi.nu, pi.nv, t, ti.dx,
+                                                ti.dy, acc);
+        else
+          forward_view<ZB, T, FDK, true, true>(img, buf, st_cur, pi.rs, pi.nu, pi.nv, t, ti.dx,
+                                               ti.dy, acc);
+      } else {
+        if (t.mode == MODE_INTERIOR)
+          forward_view<ZB, T, FDK, false, false>(img, buf, st_cur, pi.rs, pi.nu, pi.nv, t, ti.dx,
+                                                 ti.dy, acc);
+        else
+          forward_view<ZB, T, FDK, true, false>(img, buf, st_cur, pi.rs, pi.nu, pi.nv, t, ti.dx,
+                                                ti.dy, acc);
+      }
+    }
+    __syncthreads();
+    st_cur = st_next;
   }
   const int i = ti.tx * TX + ti.lx, j = ti.ty * TY + ti.ly;
   if (i < vi.nx && j < vi.ny) {
@@ -262,27 +445,41 @@ __global__ void __launch_bounds__(NT, 2)
 constexpr int ZB_FWD = 16;
 constexpr int ZB_VJP = 16;
 
+// Staging needs 16-byte aligned rows and whole 16-byte chunks per row.
+template <typename T>
+static bool stageable(const void* proj, const ProjInfo& pi) {
+  const long long es = (long long)sizeof(T), ch = 16 / es;
+  return ((reinterpret_cast<uintptr_t>(proj) & 15) == 0) && (pi.rs * es) % 16 == 0 &&
+         (pi.vs * es) % 16 == 0 && pi.nu % ch == 0;
+}
+
 template <typename T, bool FDK>
-static void forward_dispatch(const void* proj, const ProjInfo& pi, const ViewGeom* geom,
-                             const VolInfo& vi, float* vol, cudaStream_t s) {
+static cudaError_t forward_dispatch(const void* proj, const ProjInfo& pi, const ViewGeom* geom,
+                                    const VolInfo& vi, float* vol, cudaStream_t s) {
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
-  forward_kernel<ZB_FWD, T, FDK><<<ntiles, NT, 0, s>>>((const T*)proj, pi, geom, vi, vol);
+  const int smem = 2 * STAGE_BYTES;
+  if (stageable<T>(proj, pi)) {
+    cudaError_t e = cudaFuncSetAttribute(forward_kernel<ZB_FWD, T, FDK, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    forward_kernel<ZB_FWD, T, FDK, true><<<ntiles, NT, smem, s>>>((const T*)proj, pi, geom, vi, vol);
+  } else {
+    forward_kernel<ZB_FWD, T, FDK, false><<<ntiles, NT, 0, s>>>((const T*)proj, pi, geom, vi, vol);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_forward(const void* proj, int dtype, const ProjInfo& pi, const ViewGeom* geom,
                            const VolInfo& vi, int fdk, float* vol, cudaStream_t s) {
   if (vi.zb != ZB_FWD) return cudaErrorInvalidValue;
-  if (dtype == 0) {
-    fdk ? forward_dispatch<float, true>(proj, pi, geom, vi, vol, s)
-        : forward_dispatch<float, false>(proj, pi, geom, vi, vol, s);
-  } else if (dtype == 1) {
-    fdk ? forward_dispatch<__half, true>(proj, pi, geom, vi, vol, s)
-        : forward_dispatch<__half, false>(proj, pi, geom, vi, vol, s);
-  } else {
-    fdk ? forward_dispatch<__nv_bfloat16, true>(proj, pi, geom, vi, vol, s)
-        : forward_dispatch<__nv_bfloat16, false>(proj, pi, geom, vi, vol, s);
-  }
-  return cudaGetLastError();
+  if (dtype == 0)
+    return fdk ? forward_dispatch<float, true>(proj, pi, geom, vi, vol, s)
+               : forward_dispatch<float, false>(proj, pi, geom, vi, vol, s);
+  if (dtype == 1)
+    return fdk ? forward_dispatch<__half, true>(proj, pi, geom, vi, vol, s)
+               : forward_dispatch<__half, false>(proj, pi, geom, vi, vol, s);
+  return fdk ? forward_dispatch<__nv_bfloat16, true>(proj, pi, geom, vi, vol, s)
+             : forward_dispatch<__nv_bfloat16, false>(proj, pi, geom, vi, vol, s);
 }
 
 // ------------------------------------------------------- gradient images
@@ -332,6 +529,29 @@ cudaError_t launch_grad_images(const void* proj, int dtype, const ProjInfo& pi, 
   return cudaGetLastError();
 }
 
+// Four bilinear-weighted scatter-adds of one sample into a [nv][nu] image
+// (global FP32 atomics; taps off the detector are dropped in EDGE mode).
+template <bool EDGE>
+__device__ __forceinline__ void scatter_sample(float* out, int nu, int nv, const Sample& s,
+                                               float sd) {
+  const float b1 = sd * s.tv, b0 = sd - b1;
+  const float w11 = b1 * s.tu, w01 = b1 - w11, w10 = b0 * s.tu, w00 = b0 - w10;
+  float* p = out + (long long)s.iv * nu + s.iu;
+  if (!EDGE) {
+    atomicAdd(p, w00);
+    atomicAdd(p + 1, w10);
+    atomicAdd(p + nu, w01);
+    atomicAdd(p + nu + 1, w11);
+  } else {
+    const bool uu0 = (unsigned)s.iu < (unsigned)nu, uu1 = (unsigned)(s.iu + 1) < (unsigned)nu;
+    const bool vv0 = (unsigned)s.iv < (unsigned)nv, vv1 = (unsigned)(s.iv + 1) < (unsigned)nv;
+    if (uu0 && vv0) atomicAdd(p, w00);
+    if (uu1 && vv0) atomicAdd(p + 1, w10);
+    if (uu0 && vv1) atomicAdd(p + nu, w01);
+    if (uu1 && vv1) atomicAdd(p + nu + 1, w11);
+  }
+}
+
 // ------------------------------------------------------- VJP w.r.t. Phat
 
 // Sum of 16 per-lane values over the warp, scattered: lane l ends with the
@@ -379,10 +599,11 @@ __device__ __forceinline__ int scatter_slot(int lane) {
 // derivative of omega = wgt r^2 adds -2 s r val to the w component.  The
 // 3x4 outer product with (dq, 1) is accumulated as S_r = sum a_r and
 // Z_r = sum a_r dz along the thread's column; dx, dy are constant per thread.
-template <int ZB, typename T, bool FDK, bool EXACT, bool EDGE>
-__device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, long long rs, int nu,
-                                         int nv, const TileView& t, float dx, float dy,
-                                         const float (&delta)[ZB], float (&S)[3], float (&Z)[3]) {
+template <int ZB, typename T, bool FDK, bool EXACT, bool EDGE, bool PROJ>
+__device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, float* pout,
+                                         long long rs, int nu, int nv, const TileView& t, float dx,
+                                         float dy, const float (&delta)[ZB], float (&S)[3],
+                                         float (&Z)[3]) {
   float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
   float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
   float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
@@ -438,14 +659,16 @@ __device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, long 
     Z[0] = fmaf(a0, dz, Z[0]);
     Z[1] = fmaf(a1, dz, Z[1]);
     Z[2] = fmaf(a2, dz, Z[2]);
+    if (PROJ && delta[k] != 0.0f)  // fused data VJP: same sample, dequantised weight
+      scatter_sample<EDGE>(pout, nu, nv, s, delta[k] * (FDK ? s.rwi * (s.rwi * t.wgtd) : t.wgtd));
   }
 }
 
-template <int ZB, typename T, bool FDK, bool EXACT>
-__global__ void __launch_bounds__(NT, 2)
+template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ>
+__global__ void __launch_bounds__(NT, VJP_MINB)
     vjp_motion_kernel(const float* __restrict__ dvol, const T* __restrict__ proj, ProjInfo pi,
                       const float2* __restrict__ grad, const ViewGeom* __restrict__ geom,
-                      VolInfo vi, float* __restrict__ partials) {
+                      VolInfo vi, float* __restrict__ partials, float* __restrict__ dproj) {
   __shared__ TileView tvs[VB];
   __shared__ float red[NT / 32][VB][12];
   const TileIdx ti = tile_index<ZB>(vi);
@@ -466,9 +689,7 @@ __global__ void __launch_bounds__(NT, 2)
   for (int j0 = 0; j0 < pi.nviews; j0 += VB) {
     const int nb = min(VB, pi.nviews - j0);
     __syncthreads();
-    if (threadIdx.x < nb)
-      setup_tile_view(tvs[threadIdx.x], geom[j0 + threadIdx.x], ti.qc, ti.half, pi.nu, pi.nv,
-                      true);
+    setup_batch(tvs, geom, j0, nb, ti, pi.nu, pi.nv, true);
     __syncthreads();
     if (any) {
       for (int b = 0; b < nb; ++b) {
@@ -477,12 +698,13 @@ __global__ void __launch_bounds__(NT, 2)
         const T* img = proj + (long long)(j0 + b) * pi.vs;
         const float2* gimg = EXACT ? nullptr : grad + (long long)(j0 + b) * pi.nv * pi.nu;
         float S[3] = {0.0f, 0.0f, 0.0f}, Z[3] = {0.0f, 0.0f, 0.0f};
+        float* pout = PROJ ? dproj + (long long)(j0 + b) * pi.nv * pi.nu : nullptr;
         if (t.mode == MODE_INTERIOR)
-          vjp_view<ZB, T, FDK, EXACT, false>(img, gimg, pi.rs, pi.nu, pi.nv, t, ti.dx, ti.dy,
-                                             delta, S, Z);
+          vjp_view<ZB, T, FDK, EXACT, false, PROJ>(img, gimg, pout, pi.rs, pi.nu, pi.nv, t, ti.dx,
+                                                   ti.dy, delta, S, Z);
         else
-          vjp_view<ZB, T, FDK, EXACT, true>(img, gimg, pi.rs, pi.nu, pi.nv, t, ti.dx, ti.dy,
-                                            delta, S, Z);
+          vjp_view<ZB, T, FDK, EXACT, true, PROJ>(img, gimg, pout, pi.rs, pi.nu, pi.nv, t, ti.dx,
+                                                  ti.dy, delta, S, Z);
         float v[16];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
@@ -517,49 +739,56 @@ __global__ void __launch_bounds__(NT, 2)
 template <typename T, bool FDK, bool EXACT>
 static void vjp_dispatch(const float* dvol, const void* proj, const ProjInfo& pi,
                          const float2* grad, const ViewGeom* geom, const VolInfo& vi,
-                         float* partials, cudaStream_t s) {
+                         float* partials, float* dproj, cudaStream_t s) {
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
-  vjp_motion_kernel<ZB_VJP, T, FDK, EXACT>
-      <<<ntiles, NT, 0, s>>>(dvol, (const T*)proj, pi, grad, geom, vi, partials);
+  if (dproj)
+    vjp_motion_kernel<ZB_VJP, T, FDK, EXACT, true>
+        <<<ntiles, NT, 0, s>>>(dvol, (const T*)proj, pi, grad, geom, vi, partials, dproj);
+  else
+    vjp_motion_kernel<ZB_VJP, T, FDK, EXACT, false>
+        <<<ntiles, NT, 0, s>>>(dvol, (const T*)proj, pi, grad, geom, vi, partials, nullptr);
 }
 
 template <typename T>
 static void vjp_dispatch_t(int fdk, int exact, const float* dvol, const void* proj,
                            const ProjInfo& pi, const float2* grad, const ViewGeom* geom,
-                           const VolInfo& vi, float* partials, cudaStream_t s) {
+                           const VolInfo& vi, float* partials, float* dproj, cudaStream_t s) {
   if (fdk) {
-    exact ? vjp_dispatch<T, true, true>(dvol, proj, pi, grad, geom, vi, partials, s)
-          : vjp_dispatch<T, true, false>(dvol, proj, pi, grad, geom, vi, partials, s);
+    exact ? vjp_dispatch<T, true, true>(dvol, proj, pi, grad, geom, vi, partials, dproj, s)
+          : vjp_dispatch<T, true, false>(dvol, proj, pi, grad, geom, vi, partials, dproj, s);
   } else {
-    exact ? vjp_dispatch<T, false, true>(dvol, proj, pi, grad, geom, vi, partials, s)
-          : vjp_dispatch<T, false, false>(dvol, proj, pi, grad, geom, vi, partials, s);
+    exact ? vjp_dispatch<T, false, true>(dvol, proj, pi, grad, geom, vi, partials, dproj, s)
+          : vjp_dispatch<T, false, false>(dvol, proj, pi, grad, geom, vi, partials, dproj, s);
   }
 }
 
 cudaError_t launch_vjp_motion(const float* dvol, const void* proj, int dtype, const ProjInfo& pi,
                               const float2* grad, const ViewGeom* geom, const VolInfo& vi,
-                              int fdk, int exact, float* partials, cudaStream_t s) {
+                              int fdk, int exact, float* partials, float* dproj, cudaStream_t s) {
   if (vi.zb != ZB_VJP) return cudaErrorInvalidValue;
   if (dtype == 0)
-    vjp_dispatch_t<float>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, s);
+    vjp_dispatch_t<float>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, dproj, s);
   else if (dtype == 1)
-    vjp_dispatch_t<__half>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, s);
+    vjp_dispatch_t<__half>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, dproj, s);
   else
-    vjp_dispatch_t<__nv_bfloat16>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, s);
+    vjp_dispatch_t<__nv_bfloat16>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, dproj, s);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------- VJP w.r.t. the data
 
-// Adjoint of Eq. 3 in d_j: every voxel-view scatters s = delta * c * omega
-// times its four bilinear weights into a contiguous [V][nv][nu] FP32 image
-// (global FP32 atomics; the caller zeroes the output first).
+// Adjoint of Eq. 3 in d_j: every voxel-view adds s = delta * c * omega times
+// its four bilinear weights to four detector pixels of a contiguous
+// [V][nv][nu] FP32 image (zeroed by the caller), with scalar global FP32
+// atomics reduced in L2.  (Measured on GB300: shared-memory FP32 atomics are
+// emulated and float4 vector atomics of mostly-zero lanes cost more L2
+// requests than scalar ones, so neither is used.)
 template <int ZB, bool FDK, bool EDGE>
-__device__ __forceinline__ void proj_view(float* out, int nu, int nv, const TileView& t,
-                                          float dx, float dy, const float (&delta)[ZB]) {
-  float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
-  float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
-  float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
+__device__ __forceinline__ void proj_view(float* out, int nu, int nv, const TileView& t, float dx,
+                                          float dy, const float (&delta)[ZB]) {
+  const float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
+  const float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
+  const float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
 #pragma unroll
   for (int k = 0; k < ZB; ++k) {
     if (delta[k] == 0.0f) continue;
@@ -567,23 +796,8 @@ __device__ __forceinline__ void proj_view(float* out, int nu, int nv, const Tile
     Sample s = locate<EDGE>(fmaf(dz, t.ru[2], u0), fmaf(dz, t.rv[2], v0), fmaf(dz, t.rw[2], w0),
                             t, nu, nv);
     if (EDGE && !s.ok) continue;
-    const float sd = delta[k] * (FDK ? s.rwi * (s.rwi * t.wgt) : t.wgt);
-    const float b1 = sd * s.tv, b0 = sd - b1;
-    const float w11 = b1 * s.tu, w01 = b1 - w11, w10 = b0 * s.tu, w00 = b0 - w10;
-    float* p = out + (long long)s.iv * nu + s.iu;
-    if (!EDGE) {
-      atomicAdd(p, w00);
-      atomicAdd(p + 1, w10);
-      atomicAdd(p + nu, w01);
-      atomicAdd(p + nu + 1, w11);
-    } else {
-      bool uu0 = (unsigned)s.iu < (unsigned)nu, uu1 = (unsigned)(s.iu + 1) < (unsigned)nu;
-      bool vv0 = (unsigned)s.iv < (unsigned)nv, vv1 = (unsigned)(s.iv + 1) < (unsigned)nv;
-      if (uu0 && vv0) atomicAdd(p, w00);
-      if (uu1 && vv0) atomicAdd(p + 1, w10);
-      if (uu0 && vv1) atomicAdd(p + nu, w01);
-      if (uu1 && vv1) atomicAdd(p + nu + 1, w11);
-    }
+    const float sd = delta[k] * (FDK ? s.rwi * (s.rwi * t.wgtd) : t.wgtd);
+    scatter_sample<EDGE>(out, nu, nv, s, sd);
   }
 }
 
@@ -608,9 +822,7 @@ __global__ void __launch_bounds__(NT, 2)
   for (int j0 = 0; j0 < pi.nviews; j0 += VB) {
     const int nb = min(VB, pi.nviews - j0);
     __syncthreads();
-    if (threadIdx.x < nb)
-      setup_tile_view(tvs[threadIdx.x], geom[j0 + threadIdx.x], ti.qc, ti.half, pi.nu, pi.nv,
-                      false);
+    setup_batch(tvs, geom, j0, nb, ti, pi.nu, pi.nv, true);
     __syncthreads();
     for (int b = 0; b < nb; ++b) {
       const TileView t = tvs[b];

@@ -168,7 +168,7 @@ def proj_desc(proj, sid=0.0, view_scale=None):
 
 
 KERNELS = ("compose", "forward", "grad_images", "vjp_motion", "reduce_chain", "vjp_proj",
-           "sharpness", "optimizer")
+           "vjp_fused", "sharpness", "optimizer")
 
 
 def set_timing(enable=True, device=None):
