@@ -194,6 +194,54 @@ int bp_adam_step(bp_ctx* ctx, int nviews, double* theta, const double* grad, dou
                  double* m2, double lr, double beta1, double beta2, double eps, int n, int gauge,
                  void* stream);
 
+/* ------------------------------------------------------------------ jobs
+ * A motion-estimation job (Sec. II-C): everything one scan needs stays on the
+ * device -- projections, gradient images, theta, optimiser state, volume and
+ * loss history -- and motion_step() replays one captured CUDA graph per
+ * iteration: compose (Eq. 1) -> backprojection (Eq. 3) -> sharpness loss ->
+ * motion VJP (Eqs. 4-5) -> FP64 reduction and chain (Eq. 2) -> update
+ * (Eq. 6 or Adam), followed by the view-mean gauge step. */
+
+typedef enum { BP_OPT_GD = 0 /* Eq. 6 */, BP_OPT_ADAM = 1 } bp_optimizer;
+
+typedef struct {
+  int optimizer;    /* bp_optimizer */
+  double lr;        /* Adam step (translations, mm) or Eq. 6 s0 for translations */
+  double lr_rot;    /* the same for rotations (rad) */
+  double decay;     /* Eq. 6 t (GD only) */
+  double beta1, beta2, eps;  /* Adam */
+  int gauge;        /* remove the per-parameter view mean after each step */
+} bp_opt_desc;
+
+typedef struct bp_job bp_job;
+
+/* Create a job: copies proj (any location; stored compactly in its dtype), P,
+ * view_weight and theta0 (NULL = zero motion) to job-owned device memory and
+ * precomputes the gradient images (CENTRAL).  max_iters bounds the loss
+ * history.  Admission: if the job's device bytes (bp_job_bytes) would take
+ * the context's live jobs beyond its HBM budget (bp_ctx_set_hbm_budget, or the
+ * device's free memory when 0) it fails with BP_ERR_OOM and allocates
+ * nothing. */
+int bp_job_create(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, const double* P,
+                  const double* view_weight, int weight, int deriv, const bp_vol_desc* vdesc,
+                  const bp_opt_desc* opt, const double* theta0, int max_iters, bp_job** out);
+/* Device bytes a job with these sizes would hold (no allocation). */
+long long bp_job_bytes_for(const bp_proj_desc* pdesc, const bp_vol_desc* vdesc, int deriv,
+                           int max_iters);
+long long bp_job_bytes(const bp_job* job);
+int bp_ctx_set_hbm_budget(bp_ctx* ctx, long long bytes);
+/* Run n_iters iterations on `stream` (asynchronous).  The first call
+ * captures the iteration graph on a job-owned stream. */
+int motion_step(bp_job* job, int n_iters, void* stream);
+/* Synchronise the device and copy theta (float64 [V][6]) and the loss
+ * history (float64 [max_iters], may be NULL) to host memory; *iters_done
+ * (may be NULL) receives the number of iterations run. */
+int bp_job_get_motion(const bp_job* job, double* theta_host, double* loss_history,
+                      int* iters_done);
+/* The job's current volume (float32, device pointer owned by the job). */
+const float* bp_job_volume(const bp_job* job);
+void bp_job_destroy(bp_job* job);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,186 +5,12 @@
 #include <string>
 #include <vector>
 
-#include "bp_gb300.h"
-#include "bp_internal.cuh"
+
+#include "bp_ctx.h"
 
 namespace {
 
-struct Buf {
-  void* p = nullptr;
-  size_t n = 0;
-};
-
-}  // namespace
-
-namespace {
-enum KernelId {
-  K_COMPOSE, K_FORWARD, K_GRAD, K_VJP_MOTION, K_REDUCE, K_VJP_PROJ, K_VJP_FUSED, K_SHARPNESS,
-  K_OPT, K_COUNT
-};
-const char* const kKernelNames[K_COUNT] = {"compose",  "forward",   "grad_images",
-                                           "vjp_motion", "reduce_chain", "vjp_proj",
-                                           "vjp_fused",  "sharpness", "optimizer"};
-struct Pending {
-  int id;
-  cudaEvent_t a, b;
-};
-}  // namespace
-
-struct bp_ctx {
-  int device = 0;
-  std::string err;
-  // kernel accounting: launch counter (always) and optional event timing
-  long long launches = 0;
-  bool timing = false;
-  std::vector<Pending> pending;
-  std::vector<cudaEvent_t> spare;
-  double total_ms[K_COUNT] = {};
-  long long count[K_COUNT] = {};
-  // workspace
-  Buf geom, grad, partials, shblk;
-  // staging of host arguments
-  Buf s_proj, s_P, s_motion, s_vw, s_scale, s_vol, s_dvol, s_out_motion, s_out_P, s_out_proj,
-      s_theta, s_grad, s_m1, s_m2, s_loss;
-};
-
-namespace {
-
-using bpk::ProjInfo;
-using bpk::ViewGeom;
-using bpk::VolInfo;
-
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
-int fail(bp_ctx* c, int code, const std::string& msg) {
-  if (c) c->err = msg;
-  return code;
-}
-
-int cuda_fail(bp_ctx* c, cudaError_t e, const char* where) {
-  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
-  cudaGetLastError();
-  return fail(c, e == cudaErrorMemoryAllocation ? BP_ERR_OOM : BP_ERR_CUDA, m);
-}
-
-#define CK(expr, where)                              \
-  do {                                               \
-    cudaError_t e_ = (expr);                         \
-    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
-  } while (0)
-
-cudaEvent_t take_event(bp_ctx* c) {
-  if (!c->spare.empty()) {
-    cudaEvent_t e = c->spare.back();
-    c->spare.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  if (cudaEventCreate(&e) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  return e;
-}
-
-// Fold finished event pairs into the per-kernel totals (synchronises them).
-void resolve_timing(bp_ctx* c) {
-  for (const Pending& p : c->pending) {
-    float ms = 0.0f;
-    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-      c->total_ms[p.id] += ms;
-      c->count[p.id] += 1;
-    } else {
-      cudaGetLastError();
-    }
-    c->spare.push_back(p.a);
-    c->spare.push_back(p.b);
-  }
-  c->pending.clear();
-}
-
-// Launch nk kernels through f(); with timing on, bracket them by events.
-template <class F>
-cudaError_t timed(bp_ctx* c, int id, int nk, cudaStream_t s, F f) {
-  c->launches += nk;
-  if (!c->timing) return f();
-  cudaEvent_t a = take_event(c), b = take_event(c);
-  if (!a || !b) return f();
-  cudaEventRecord(a, s);
-  cudaError_t e = f();
-  cudaEventRecord(b, s);
-  c->pending.push_back({id, a, b});
-  if (c->pending.size() > 4096) resolve_timing(c);
-  return e;
-}
-
-#define TL(id, nk, expr) timed(ctx, id, nk, s, [&]() { return (expr); })
-
-// Grow a workspace buffer (contents are not preserved).
-cudaError_t ensure(Buf& b, size_t bytes) {
-  if (bytes == 0) bytes = 16;
-  if (b.n >= bytes) return cudaSuccess;
-  if (b.p) {
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return e;
-    cudaFree(b.p);
-    b.p = nullptr;
-    b.n = 0;
-  }
-  cudaError_t e = cudaMalloc(&b.p, bytes);
-  if (e != cudaSuccess) {
-    b.p = nullptr;
-    return e;
-  }
-  b.n = bytes;
-  return cudaSuccess;
-}
-
-bool is_host(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes a;
-  cudaError_t e = cudaPointerGetAttributes(&a, p);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return true;
-  }
-  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
-}
-
-// Returns a device pointer holding `bytes` of the caller's array (copied to
-// `stage` when the caller's pointer is host memory).
-cudaError_t stage_in(Buf& stage, const void* p, size_t bytes, cudaStream_t s, const void** out) {
-  if (!p || !is_host(p)) {
-    *out = p;
-    return cudaSuccess;
-  }
-  cudaError_t e = ensure(stage, bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(stage.p, p, bytes, cudaMemcpyHostToDevice, s);
-  *out = stage.p;
-  return e;
-}
-
-// Device destination for an output (a staging buffer when it is host memory).
-cudaError_t stage_out(Buf& stage, void* p, size_t bytes, void** out, bool* host) {
-  *host = p && is_host(p);
-  if (!*host) {
-    *out = p;
-    return cudaSuccess;
-  }
-  cudaError_t e = ensure(stage, bytes);
-  *out = stage.p;
-  return e;
-}
+using namespace bpctx;
 
 size_t dtype_size(int dt) { return dt == BP_F32 ? 4 : 2; }
 

@@ -315,4 +315,91 @@ cudaError_t launch_adam(int V, double* theta, const double* grad, double* m1, do
   return cudaGetLastError();
 }
 
+// ------------------------------------------- graph-replayable (device counter)
+
+// The job loop replays one captured CUDA graph per iteration, so iteration
+// numbers live on the device: the loss goes to history[*iter], the update
+// reads *iter and advances it.
+
+__global__ void sharpness_finish_hist_kernel(const double* __restrict__ block_sums, int nb,
+                                             double K, double* __restrict__ history,
+                                             const int* __restrict__ iter, int hist_len) {
+  __shared__ double red[SH_THREADS];
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += block_sums[b];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = SH_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int it = *iter;
+    if (it >= 0 && it < hist_len) history[it] = -red[0] / K;
+  }
+}
+
+cudaError_t launch_sharpness_hist(const float* vol, int nx, int ny, int nz, double* block_sums,
+                                  int max_blocks, double* history, const int* iter, int hist_len,
+                                  float* grad, cudaStream_t s) {
+  long long nvox = (long long)nx * ny * nz;
+  int nb = sharpness_blocks(nvox);
+  if (nb > max_blocks) nb = max_blocks;
+  sharpness_kernel<<<nb, SH_THREADS, 0, s>>>(vol, nx, ny, nz, block_sums, grad);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  sharpness_finish_hist_kernel<<<1, SH_THREADS, 0, s>>>(block_sums, nb, (double)nvox, history, iter,
+                                                         hist_len);
+  return cudaGetLastError();
+}
+
+// Adam with separate step sizes for translations (mm) and rotations (rad);
+// n = *iter + 1.
+__global__ void adam_dev_kernel(int V, double* theta, const double* grad, double* m1, double* m2,
+                                double lr_t, double lr_r, double b1, double b2, double eps,
+                                int* iter, int gauge) {
+  const int n = *iter + 1;
+  const double c1 = 1.0 - pow(b1, (double)n), c2 = 1.0 - pow(b2, (double)n);
+  for (int e = threadIdx.x; e < 6 * V; e += blockDim.x) {
+    const double g = grad[e];
+    const double a = b1 * m1[e] + (1.0 - b1) * g;
+    const double b = b2 * m2[e] + (1.0 - b2) * g * g;
+    m1[e] = a;
+    m2[e] = b;
+    const double lr = (e % 6) < 3 ? lr_t : lr_r;
+    theta[e] -= lr * (a / c1) / (sqrt(b / c2) + eps);
+  }
+  __syncthreads();
+  if (gauge) remove_mean(V, theta);
+  if (threadIdx.x == 0) *iter = n;
+}
+
+// Eq. 6 with step s0 * t^n (n = *iter, starting at 0), separate s0 for
+// translations and rotations.
+__global__ void gd_dev_kernel(int V, double* theta, const double* grad, double s0_t, double s0_r,
+                              double t, int* iter, int gauge) {
+  const int n = *iter;
+  const double f = pow(t, (double)n);
+  for (int e = threadIdx.x; e < 6 * V; e += blockDim.x)
+    theta[e] -= ((e % 6) < 3 ? s0_t : s0_r) * f * grad[e];
+  __syncthreads();
+  if (gauge) remove_mean(V, theta);
+  if (threadIdx.x == 0) *iter = n + 1;
+}
+
+cudaError_t launch_adam_dev(int V, double* theta, const double* grad, double* m1, double* m2,
+                            double lr_t, double lr_r, double b1, double b2, double eps, int* iter,
+                            int gauge, cudaStream_t s) {
+  if (V <= 0) return cudaSuccess;
+  adam_dev_kernel<<<1, 256, 0, s>>>(V, theta, grad, m1, m2, lr_t, lr_r, b1, b2, eps, iter, gauge);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gd_dev(int V, double* theta, const double* grad, double s0_t, double s0_r,
+                          double t, int* iter, int gauge, cudaStream_t s) {
+  if (V <= 0) return cudaSuccess;
+  gd_dev_kernel<<<1, 256, 0, s>>>(V, theta, grad, s0_t, s0_r, t, iter, gauge);
+  return cudaGetLastError();
+}
+
 }  // namespace bpk

@@ -73,6 +73,9 @@ cudaError_t launch_compose(const double* P, const double* theta, const double* v
 
 cudaError_t launch_forward(const void* proj, int dtype, const ProjInfo& pi, const ViewGeom* geom,
                            const VolInfo& vi, int fdk, float* vol, cudaStream_t s);
+// Set the forward kernel's shared-memory attribute on the current device
+// (done by the first launch anyway; call before capturing a graph).
+cudaError_t prepare_forward(int dtype, int fdk);
 
 cudaError_t launch_grad_images(const void* proj, int dtype, const ProjInfo& pi, float2* grad,
                                cudaStream_t s);
@@ -101,5 +104,15 @@ cudaError_t launch_adam(int V, double* theta, const double* grad, double* m1, do
                         cudaStream_t s);
 
 int sharpness_blocks(long long nvox);
+
+// Graph-replayable variants: the iteration number lives on the device.
+cudaError_t launch_sharpness_hist(const float* vol, int nx, int ny, int nz, double* block_sums,
+                                  int max_blocks, double* history, const int* iter, int hist_len,
+                                  float* grad, cudaStream_t s);
+cudaError_t launch_adam_dev(int V, double* theta, const double* grad, double* m1, double* m2,
+                            double lr_t, double lr_r, double b1, double b2, double eps, int* iter,
+                            int gauge, cudaStream_t s);
+cudaError_t launch_gd_dev(int V, double* theta, const double* grad, double s0_t, double s0_r,
+                          double t, int* iter, int gauge, cudaStream_t s);
 
 }  // namespace bpk

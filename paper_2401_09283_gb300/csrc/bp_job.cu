@@ -1,0 +1,320 @@
+// Motion-estimation jobs (C-ABI in include/bp_gb300.h): device-resident
+// state and one captured CUDA graph per iteration of the gradient-based
+// motion estimation of Sec. II-C (compose -> backprojection -> loss -> VJP ->
+// FP64 reduction and chain rule -> optimiser update).
+#include "bp_ctx.h"
+
+using namespace bpctx;
+
+struct bp_job {
+  bp_ctx* ctx = nullptr;
+  int device = 0;
+  bp_proj_desc pd{};
+  bp_vol_desc vd{};
+  bp_opt_desc opt{};
+  int weight = 0, deriv = 0, max_iters = 0;
+  bpk::VolInfo vi{};
+  bpk::ProjInfo pi{};
+  int ntiles = 0, nblk = 0;
+  void* base = nullptr;  // one allocation, carved below
+  void* proj = nullptr;
+  float* scale = nullptr;
+  double *P = nullptr, *vw = nullptr, *theta = nullptr, *m1 = nullptr, *m2 = nullptr,
+         *gth = nullptr, *blk = nullptr, *hist = nullptr;
+  bpk::ViewGeom* geom = nullptr;
+  float2* grad = nullptr;
+  float *partials = nullptr, *vol = nullptr, *dvol = nullptr;
+  int* iter = nullptr;
+  long long bytes = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+constexpr int ZB = 16;
+constexpr long long kAlign = 256;
+
+long long align_up(long long x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// The job's buffers in allocation order (sizes in bytes).
+struct Layout {
+  long long proj, scale, P, vw, theta, m1, m2, gth, geom, grad, partials, vol, dvol, blk, hist,
+      iter, total;
+};
+
+Layout layout(const bp_proj_desc* pd, const bp_vol_desc* vd, int deriv, int max_iters) {
+  Layout L;
+  const long long V = pd->nviews, npx = (long long)pd->nu * pd->nv;
+  const long long nvox = (long long)vd->nx * vd->ny * vd->nz;
+  const long long tiles = (long long)((vd->nx + 15) / 16) * ((vd->ny + 15) / 16) * ((vd->nz + ZB - 1) / ZB);
+  L.proj = align_up(V * npx * (pd->dtype == BP_F32 ? 4 : 2));
+  L.scale = align_up(V * 4);
+  L.P = align_up(V * 96);
+  L.vw = align_up(V * 8);
+  L.theta = L.m1 = L.m2 = L.gth = align_up(V * 48);
+  L.geom = align_up(V * (long long)sizeof(bpk::ViewGeom));
+  L.grad = deriv == BP_DERIV_CENTRAL ? align_up(V * npx * 8) : 0;
+  L.partials = align_up(V * tiles * bpk::PSLOTS * 4);
+  L.vol = L.dvol = align_up(nvox * 4);
+  L.blk = align_up(bpk::sharpness_blocks(nvox) * 8LL);
+  L.hist = align_up((long long)max_iters * 8);
+  L.iter = kAlign;
+  L.total = L.proj + L.scale + L.P + L.vw + 4 * L.theta + L.geom + L.grad + L.partials +
+            2 * L.vol + L.blk + L.hist + L.iter;
+  return L;
+}
+
+void release(bp_job* j) {
+  if (j->exec) cudaGraphExecDestroy(j->exec);
+  if (j->graph) cudaGraphDestroy(j->graph);
+  if (j->cap) cudaStreamDestroy(j->cap);
+  if (j->base) cudaFree(j->base);
+  j->exec = nullptr;
+  j->graph = nullptr;
+  j->cap = nullptr;
+  j->base = nullptr;
+}
+
+// Record one iteration on stream s.
+cudaError_t record_iteration(bp_job* j, cudaStream_t s) {
+  const int fdk = j->weight == BP_WEIGHT_FDK;
+  const int V = j->pd.nviews;
+  cudaError_t e;
+  e = bpk::launch_compose(j->P, j->theta, j->vw, j->scale, V, fdk, j->pd.sid, j->vi, j->geom,
+                          nullptr, s);
+  if (e != cudaSuccess) return e;
+  e = bpk::launch_forward(j->proj, j->pd.dtype, j->pi, j->geom, j->vi, fdk, j->vol, s);
+  if (e != cudaSuccess) return e;
+  e = bpk::launch_sharpness_hist(j->vol, j->vd.nx, j->vd.ny, j->vd.nz, j->blk, j->nblk, j->hist,
+                                 j->iter, j->max_iters, j->dvol, s);
+  if (e != cudaSuccess) return e;
+  e = bpk::launch_vjp_motion(j->dvol, j->proj, j->pd.dtype, j->pi, j->grad, j->geom, j->vi, fdk,
+                             j->deriv == BP_DERIV_BILINEAR_EXACT, j->partials, nullptr, s);
+  if (e != cudaSuccess) return e;
+  e = bpk::launch_reduce_chain(j->partials, j->ntiles, j->vi, j->P, j->theta, V, nullptr, j->gth,
+                               s);
+  if (e != cudaSuccess) return e;
+  if (j->opt.optimizer == BP_OPT_ADAM)
+    return bpk::launch_adam_dev(V, j->theta, j->gth, j->m1, j->m2, j->opt.lr, j->opt.lr_rot,
+                                j->opt.beta1, j->opt.beta2, j->opt.eps, j->iter, j->opt.gauge, s);
+  return bpk::launch_gd_dev(V, j->theta, j->gth, j->opt.lr, j->opt.lr_rot, j->opt.decay, j->iter,
+                            j->opt.gauge, s);
+}
+
+constexpr int kKernelsPerIteration = 7;  // compose, forward, 2 loss, VJP, reduce, update
+
+}  // namespace
+
+extern "C" {
+
+long long bp_job_bytes_for(const bp_proj_desc* pdesc, const bp_vol_desc* vdesc, int deriv,
+                           int max_iters) {
+  if (!pdesc || !vdesc || max_iters < 0) return -1;
+  return layout(pdesc, vdesc, deriv, max_iters).total;
+}
+
+long long bp_job_bytes(const bp_job* job) { return job ? job->bytes : 0; }
+
+int bp_ctx_set_hbm_budget(bp_ctx* ctx, long long bytes) {
+  if (!ctx || bytes < 0) return BP_ERR_INVALID_ARG;
+  ctx->hbm_budget = bytes;
+  return BP_OK;
+}
+
+int bp_job_create(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, const double* P,
+                  const double* view_weight, int weight, int deriv, const bp_vol_desc* vdesc,
+                  const bp_opt_desc* opt, const double* theta0, int max_iters, bp_job** out) {
+  if (!ctx || !out) return BP_ERR_INVALID_ARG;
+  *out = nullptr;
+  ctx->err.clear();
+  if (!pdesc || !vdesc || !opt || !proj || !P)
+    return fail(ctx, BP_ERR_INVALID_ARG, "bp_job_create: NULL argument");
+  if (pdesc->nu < 1 || pdesc->nv < 1 || pdesc->nviews < 1 || vdesc->nx < 1 || vdesc->ny < 1 ||
+      vdesc->nz < 1 || max_iters < 0)
+    return fail(ctx, BP_ERR_INVALID_ARG, "bp_job_create: empty problem or negative max_iters");
+  if (pdesc->dtype != BP_F32 && pdesc->dtype != BP_F16 && pdesc->dtype != BP_BF16)
+    return fail(ctx, BP_ERR_INVALID_ARG, "bp_job_create: unknown dtype");
+  if (pdesc->row_stride < pdesc->nu || pdesc->view_stride < (long long)pdesc->nv * pdesc->row_stride)
+    return fail(ctx, BP_ERR_INVALID_ARG, "bp_job_create: bad strides");
+  if ((weight != BP_WEIGHT_NONE && weight != BP_WEIGHT_FDK) ||
+      (deriv != BP_DERIV_CENTRAL && deriv != BP_DERIV_BILINEAR_EXACT) ||
+      (opt->optimizer != BP_OPT_GD && opt->optimizer != BP_OPT_ADAM))
+    return fail(ctx, BP_ERR_INVALID_ARG, "bp_job_create: unknown weight/deriv/optimizer");
+  DeviceGuard g(ctx->device);
+  const Layout L = layout(pdesc, vdesc, deriv, max_iters);
+  // admission by device memory
+  long long avail;
+  if (ctx->hbm_budget > 0) {
+    avail = ctx->hbm_budget - ctx->job_bytes;
+  } else {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "meminfo");
+    avail = (long long)fr - (256LL << 20);
+  }
+  if (L.total > avail)
+    return fail(ctx, BP_ERR_OOM, "bp_job_create: job needs " + std::to_string(L.total) +
+                                     " bytes, " + std::to_string(avail > 0 ? avail : 0) +
+                                     " available under the budget");
+  bp_job* j = new bp_job();
+  j->ctx = ctx;
+  j->device = ctx->device;
+  j->pd = *pdesc;
+  j->vd = *vdesc;
+  j->opt = *opt;
+  j->weight = weight;
+  j->deriv = deriv;
+  j->max_iters = max_iters;
+  j->bytes = L.total;
+  cudaError_t e = cudaMalloc(&j->base, (size_t)L.total);
+  if (e != cudaSuccess) {
+    delete j;
+    return cuda_fail(ctx, e, "bp_job_create: cudaMalloc");
+  }
+  char* p = (char*)j->base;
+  auto take = [&](long long n) {
+    char* q = p;
+    p += n;
+    return (void*)q;
+  };
+  j->proj = take(L.proj);
+  j->scale = (float*)take(L.scale);
+  j->P = (double*)take(L.P);
+  j->vw = (double*)take(L.vw);
+  j->theta = (double*)take(L.theta);
+  j->m1 = (double*)take(L.m1);
+  j->m2 = (double*)take(L.m2);
+  j->gth = (double*)take(L.gth);
+  j->geom = (bpk::ViewGeom*)take(L.geom);
+  j->grad = L.grad ? (float2*)take(L.grad) : nullptr;
+  j->partials = (float*)take(L.partials);
+  j->vol = (float*)take(L.vol);
+  j->dvol = (float*)take(L.dvol);
+  j->blk = (double*)take(L.blk);
+  j->hist = (double*)take(L.hist);
+  j->iter = (int*)take(L.iter);
+  const int V = pdesc->nviews;
+  const size_t es = pdesc->dtype == BP_F32 ? 4 : 2;
+  // inputs (host or device: cudaMemcpyDefault under unified addressing)
+  e = cudaMemcpy2D(j->proj, es * pdesc->nu, proj, es * pdesc->row_stride, es * pdesc->nu,
+                   (size_t)pdesc->nv, cudaMemcpyDefault);
+  for (int v = 1; v < V && e == cudaSuccess; ++v)
+    e = cudaMemcpy2D((char*)j->proj + es * (size_t)v * pdesc->nu * pdesc->nv, es * pdesc->nu,
+                     (const char*)proj + es * (size_t)v * pdesc->view_stride,
+                     es * pdesc->row_stride, es * pdesc->nu, (size_t)pdesc->nv, cudaMemcpyDefault);
+  if (e == cudaSuccess) e = cudaMemcpy(j->P, P, 96 * (size_t)V, cudaMemcpyDefault);
+  if (e == cudaSuccess) {
+    if (view_weight) e = cudaMemcpy(j->vw, view_weight, 8 * (size_t)V, cudaMemcpyDefault);
+    else j->vw = nullptr;
+  }
+  if (e == cudaSuccess) {
+    if (pdesc->view_scale) e = cudaMemcpy(j->scale, pdesc->view_scale, 4 * (size_t)V, cudaMemcpyDefault);
+    else j->scale = nullptr;
+  }
+  if (e == cudaSuccess) {
+    if (theta0) e = cudaMemcpy(j->theta, theta0, 48 * (size_t)V, cudaMemcpyDefault);
+    else e = cudaMemset(j->theta, 0, 48 * (size_t)V);
+  }
+  if (e == cudaSuccess) e = cudaMemset(j->m1, 0, 48 * (size_t)V);
+  if (e == cudaSuccess) e = cudaMemset(j->m2, 0, 48 * (size_t)V);
+  if (e == cudaSuccess) e = cudaMemset(j->iter, 0, sizeof(int));
+  if (e == cudaSuccess && max_iters > 0) e = cudaMemset(j->hist, 0, 8 * (size_t)max_iters);
+  j->pd.row_stride = pdesc->nu;
+  j->pd.view_stride = (long long)pdesc->nu * pdesc->nv;
+  j->pd.view_scale = j->scale;
+  j->vi.nx = vdesc->nx;
+  j->vi.ny = vdesc->ny;
+  j->vi.nz = vdesc->nz;
+  j->vi.zb = ZB;
+  j->vi.tiles_x = (vdesc->nx + 15) / 16;
+  j->vi.tiles_y = (vdesc->ny + 15) / 16;
+  j->vi.tiles_z = (vdesc->nz + ZB - 1) / ZB;
+  j->vi.cx = 0.5 * (vdesc->nx - 1);
+  j->vi.cy = 0.5 * (vdesc->ny - 1);
+  j->vi.cz = 0.5 * (vdesc->nz - 1);
+  const double c[3] = {j->vi.cx, j->vi.cy, j->vi.cz};
+  for (int k = 0; k < 12; ++k) j->vi.A[k] = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    j->vi.A[4 * a + a] = vdesc->spacing[a];
+    j->vi.A[4 * a + 3] = vdesc->origin[a] + c[a] * vdesc->spacing[a];
+  }
+  j->pi.nu = pdesc->nu;
+  j->pi.nv = pdesc->nv;
+  j->pi.nviews = V;
+  j->pi.rs = pdesc->nu;
+  j->pi.vs = (long long)pdesc->nu * pdesc->nv;
+  j->ntiles = j->vi.tiles_x * j->vi.tiles_y * j->vi.tiles_z;
+  j->nblk = bpk::sharpness_blocks((long long)vdesc->nx * vdesc->ny * vdesc->nz);
+  if (e == cudaSuccess && j->grad) {
+    e = bpk::launch_grad_images(j->proj, pdesc->dtype, j->pi, j->grad, nullptr);
+    ctx->launches += 1;
+  }
+  if (e == cudaSuccess) e = bpk::prepare_forward(pdesc->dtype, weight == BP_WEIGHT_FDK);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    release(j);
+    delete j;
+    return cuda_fail(ctx, e, "bp_job_create");
+  }
+  ctx->job_bytes += j->bytes;
+  *out = j;
+  return BP_OK;
+}
+
+int motion_step(bp_job* j, int n_iters, void* stream) {
+  if (!j || n_iters < 0) return BP_ERR_INVALID_ARG;
+  bp_ctx* ctx = j->ctx;
+  ctx->err.clear();
+  if (n_iters == 0) return BP_OK;
+  DeviceGuard g(j->device);
+  if (!j->exec) {
+    cudaError_t e = cudaStreamCreateWithFlags(&j->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(j->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "motion_step: capture");
+    cudaError_t le = record_iteration(j, j->cap);
+    e = cudaStreamEndCapture(j->cap, &j->graph);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&j->exec, j->graph, 0);
+    if (e != cudaSuccess) {
+      if (j->graph) cudaGraphDestroy(j->graph);
+      j->graph = nullptr;
+      j->exec = nullptr;
+      return cuda_fail(ctx, e, "motion_step: graph");
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < n_iters; ++i) {
+    cudaError_t e = cudaGraphLaunch(j->exec, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "motion_step: launch");
+  }
+  ctx->launches += (long long)kKernelsPerIteration * n_iters;
+  return BP_OK;
+}
+
+int bp_job_get_motion(const bp_job* j, double* theta_host, double* loss_history,
+                      int* iters_done) {
+  if (!j) return BP_ERR_INVALID_ARG;
+  DeviceGuard g(j->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && theta_host)
+    e = cudaMemcpy(theta_host, j->theta, 48 * (size_t)j->pd.nviews, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && loss_history && j->max_iters > 0)
+    e = cudaMemcpy(loss_history, j->hist, 8 * (size_t)j->max_iters, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && iters_done) e = cudaMemcpy(iters_done, j->iter, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(j->ctx, e, "bp_job_get_motion");
+  return BP_OK;
+}
+
+const float* bp_job_volume(const bp_job* j) { return j ? j->vol : nullptr; }
+
+void bp_job_destroy(bp_job* j) {
+  if (!j) return;
+  DeviceGuard g(j->device);
+  cudaDeviceSynchronize();
+  j->ctx->job_bytes -= j->bytes;
+  release(j);
+  delete j;
+}
+
+}  // extern "C"

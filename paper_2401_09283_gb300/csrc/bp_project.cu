@@ -453,20 +453,45 @@ static bool stageable(const void* proj, const ProjInfo& pi) {
          (pi.vs * es) % 16 == 0 && pi.nu % ch == 0;
 }
 
+// Opt a kernel into more than 48 KiB of dynamic shared memory, once per
+// device (so that later launches -- including ones being captured into a
+// CUDA graph -- make no attribute call).
+template <auto Kernel>
+static cudaError_t smem_attr_once(int bytes) {
+  static int done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaGetLastError();
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
+  return e;
+}
+
 template <typename T, bool FDK>
 static cudaError_t forward_dispatch(const void* proj, const ProjInfo& pi, const ViewGeom* geom,
                                     const VolInfo& vi, float* vol, cudaStream_t s) {
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
   const int smem = 2 * STAGE_BYTES;
   if (stageable<T>(proj, pi)) {
-    cudaError_t e = cudaFuncSetAttribute(forward_kernel<ZB_FWD, T, FDK, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = smem_attr_once<forward_kernel<ZB_FWD, T, FDK, true>>(smem);
     if (e != cudaSuccess) return e;
     forward_kernel<ZB_FWD, T, FDK, true><<<ntiles, NT, smem, s>>>((const T*)proj, pi, geom, vi, vol);
   } else {
     forward_kernel<ZB_FWD, T, FDK, false><<<ntiles, NT, 0, s>>>((const T*)proj, pi, geom, vi, vol);
   }
   return cudaGetLastError();
+}
+
+cudaError_t prepare_forward(int dtype, int fdk) {
+  const int smem = 2 * STAGE_BYTES;
+  if (dtype == 0)
+    return fdk ? smem_attr_once<forward_kernel<ZB_FWD, float, true, true>>(smem)
+               : smem_attr_once<forward_kernel<ZB_FWD, float, false, true>>(smem);
+  if (dtype == 1)
+    return fdk ? smem_attr_once<forward_kernel<ZB_FWD, __half, true, true>>(smem)
+               : smem_attr_once<forward_kernel<ZB_FWD, __half, false, true>>(smem);
+  return fdk ? smem_attr_once<forward_kernel<ZB_FWD, __nv_bfloat16, true, true>>(smem)
+             : smem_attr_once<forward_kernel<ZB_FWD, __nv_bfloat16, false, true>>(smem);
 }
 
 cudaError_t launch_forward(const void* proj, int dtype, const ProjInfo& pi, const ViewGeom* geom,

@@ -1,0 +1,89 @@
+"""Motion-estimation jobs (Sec. II-C) through the C-ABI job entry points.
+
+A job owns device copies of the projections and all optimiser state;
+motion_step() replays one captured CUDA graph per iteration (compose ->
+backprojection -> sharpness loss -> motion VJP -> FP64 reduction and chain
+rule -> Adam or the decaying gradient step of Eq. 6)."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import native as N
+
+OPT = {"gd": 0, "adam": 1}
+
+
+class MotionJob:
+    def __init__(self, proj, P, *, vol_shape, spacing, origin, sid, view_weight=None,
+                 weight="fdk", deriv="central", optimizer="adam", lr=0.1, lr_rot=1e-3,
+                 decay=0.97, betas=(0.9, 0.999), eps=1e-8, gauge=True, theta0=None,
+                 max_iters=100, view_scale=None, device=None):
+        self.V = int(P.shape[0])
+        self.max_iters = int(max_iters)
+        if device is None:
+            device = N.device_of(proj, P)
+        self.device = device
+        self.ctx = N.context(device)
+        pd = N.proj_desc(proj, sid, view_scale)
+        vd = N.vol_desc(vol_shape, spacing, origin)
+        od = N.OptDesc(OPT[optimizer], float(lr), float(lr_rot), float(decay), float(betas[0]),
+                       float(betas[1]), float(eps), int(bool(gauge)))
+        Pc = P if isinstance(P, torch.Tensor) else torch.as_tensor(np.ascontiguousarray(P))
+        self._keep = (proj, Pc, view_weight, theta0, view_scale)
+        h = ctypes.c_void_p()
+        rc = N.lib().bp_job_create(self.ctx, N.ptr(proj), ctypes.byref(pd), N.ptr(Pc),
+                                   N.ptr(view_weight), N.WEIGHT[weight], N.DERIV[deriv],
+                                   ctypes.byref(vd), ctypes.byref(od), N.ptr(theta0),
+                                   self.max_iters, ctypes.byref(h))
+        N.check("bp_job_create", rc, self.ctx)
+        self.handle = h
+        self._keep = None
+
+    @staticmethod
+    def bytes_for(proj_shape, dtype_code, vol_shape, deriv="central", max_iters=100):
+        V, nv, nu = proj_shape
+        pd = N.ProjDesc(nu, nv, V, dtype_code, nu, nu * nv, None, 0.0)
+        vd = N.vol_desc(vol_shape, (1, 1, 1), (0, 0, 0))
+        return int(N.lib().bp_job_bytes_for(ctypes.byref(pd), ctypes.byref(vd), N.DERIV[deriv],
+                                            int(max_iters)))
+
+    @property
+    def nbytes(self):
+        return int(N.lib().bp_job_bytes(self.handle))
+
+    def step(self, n=1, stream=None):
+        """Queue n iterations on `stream` (default: the current torch stream)."""
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        rc = N.lib().motion_step(self.handle, int(n), stream)
+        N.check("motion_step", rc, self.ctx)
+
+    def motion(self):
+        """(theta (V,6), loss history (max_iters,), iterations done) on the host."""
+        th = np.zeros((self.V, 6))
+        hist = np.zeros(max(1, self.max_iters))
+        it = ctypes.c_int()
+        rc = N.lib().bp_job_get_motion(self.handle, th.ctypes.data, hist.ctypes.data,
+                                       ctypes.byref(it))
+        N.check("bp_job_get_motion", rc, self.ctx)
+        return th, hist[: self.max_iters], int(it.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.lib().bp_job_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def set_hbm_budget(nbytes, device=None):
+    """Bytes that the live jobs of a device's context may hold (0 = free memory)."""
+    ctx = N.context(device)
+    N.check("bp_ctx_set_hbm_budget", N.lib().bp_ctx_set_hbm_budget(ctx, int(nbytes)), ctx)

@@ -37,6 +37,11 @@ class ProjDesc(ctypes.Structure):
                 ("sid", c_double)]
 
 
+class OptDesc(ctypes.Structure):
+    _fields_ = [("optimizer", c_int), ("lr", c_double), ("lr_rot", c_double), ("decay", c_double),
+                ("beta1", c_double), ("beta2", c_double), ("eps", c_double), ("gauge", c_int)]
+
+
 class BPError(RuntimeError):
     def __init__(self, fn, code, msg):
         super().__init__("%s failed: %s (%d): %s" % (fn, STATUS.get(code, "?"), code, msg))
@@ -50,7 +55,9 @@ _ctx = {}
 EXPORTS = ["bp_ctx_create", "bp_ctx_destroy", "bp_last_error", "bp_ctx_workspace_bytes",
            "bp_ctx_launch_count", "bp_ctx_set_timing", "bp_ctx_timing",
            "bp_compose", "bp_forward", "bp_vjp", "bp_sharpness", "bp_sharpness_noalloc",
-           "bp_gd_step", "bp_adam_step"]
+           "bp_gd_step", "bp_adam_step", "bp_job_create", "bp_job_bytes_for", "bp_job_bytes",
+           "bp_ctx_set_hbm_budget", "motion_step", "bp_job_get_motion", "bp_job_volume",
+           "bp_job_destroy"]
 
 
 def lib():
@@ -88,6 +95,21 @@ def lib():
                 L.bp_gd_step.argtypes = [vp, c_int, vp, vp, c_double, c_double, c_int, c_int, vp]
                 L.bp_adam_step.argtypes = [vp, c_int, vp, vp, vp, vp, c_double, c_double,
                                            c_double, c_double, c_int, c_int, vp]
+                L.bp_job_create.argtypes = [vp, vp, ctypes.POINTER(ProjDesc), vp, vp, c_int, c_int,
+                                            ctypes.POINTER(VolDesc), ctypes.POINTER(OptDesc), vp,
+                                            c_int, ctypes.POINTER(c_void_p)]
+                L.bp_job_bytes_for.argtypes = [ctypes.POINTER(ProjDesc), ctypes.POINTER(VolDesc),
+                                               c_int, c_int]
+                L.bp_job_bytes_for.restype = c_ll
+                L.bp_job_bytes.argtypes = [vp]
+                L.bp_job_bytes.restype = c_ll
+                L.bp_ctx_set_hbm_budget.argtypes = [vp, c_ll]
+                L.motion_step.argtypes = [vp, c_int, vp]
+                L.bp_job_get_motion.argtypes = [vp, vp, vp, ctypes.POINTER(c_int)]
+                L.bp_job_volume.argtypes = [vp]
+                L.bp_job_volume.restype = c_void_p
+                L.bp_job_destroy.argtypes = [vp]
+                L.bp_job_destroy.restype = None
                 _lib = L
     return _lib
 
