@@ -47,6 +47,8 @@ struct TileView {
   int mode;           // MODE_*
   int fu0, fv0;       // detector footprint of the tile (first pixel), clipped
   int fw, fh;         // footprint size in pixels (0 when unbounded)
+  int csafe;          // every tap pixel and its central-difference neighbours
+                      // (one more pixel each side) lie inside the detector
 };
 
 enum { MODE_SKIP = 0, MODE_INTERIOR = 1, MODE_EDGE = 2 };
@@ -73,9 +75,11 @@ cudaError_t launch_compose(const double* P, const double* theta, const double* v
 
 cudaError_t launch_forward(const void* proj, int dtype, const ProjInfo& pi, const ViewGeom* geom,
                            const VolInfo& vi, int fdk, float* vol, cudaStream_t s);
-// Set the forward kernel's shared-memory attribute on the current device
-// (done by the first launch anyway; call before capturing a graph).
+// Set the forward / motion-VJP kernels' shared-memory attributes on the
+// current device (done by the first launch anyway; call before capturing a
+// graph).
 cudaError_t prepare_forward(int dtype, int fdk);
+cudaError_t prepare_vjp(int dtype, int fdk, int exact);
 
 cudaError_t launch_grad_images(const void* proj, int dtype, const ProjInfo& pi, float2* grad,
                                cudaStream_t s);

@@ -251,6 +251,8 @@ int bp_job_create(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, cons
     ctx->launches += 1;
   }
   if (e == cudaSuccess) e = bpk::prepare_forward(pdesc->dtype, weight == BP_WEIGHT_FDK);
+  if (e == cudaSuccess)
+    e = bpk::prepare_vjp(pdesc->dtype, weight == BP_WEIGHT_FDK, deriv == BP_DERIV_BILINEAR_EXACT);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     release(j);

@@ -60,12 +60,11 @@ struct TileIdx {
 };
 
 template <int ZB>
-__device__ __forceinline__ TileIdx tile_index(const VolInfo& vi) {
+__device__ __forceinline__ TileIdx tile_index(const VolInfo& vi, int tile) {
   TileIdx ti;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   ti.lx = (warp & 1) * 8 + (lane & 7);
   ti.ly = (warp >> 1) * 4 + (lane >> 3);
-  const int tile = blockIdx.x;
   ti.tx = tile % vi.tiles_x;
   ti.ty = (tile / vi.tiles_x) % vi.tiles_y;
   ti.tz = tile / (vi.tiles_x * vi.tiles_y);
@@ -154,6 +153,7 @@ __device__ void setup_batch(TileView* tvs, const ViewGeom* __restrict__ geom, in
   // detector [0, n-1] in the anchored frame
   const float ulo = -fau, uhi = (float)(nu - 1) - fau, vlo = -fav, vhi = (float)(nv - 1) - fav;
   t.fu0 = t.fv0 = t.fw = t.fh = 0;
+  t.csafe = 0;
   if (npos == 0) {
     t.mode = MODE_SKIP;
   } else if (npos < 8) {
@@ -165,6 +165,10 @@ __device__ void setup_batch(TileView* tvs, const ViewGeom* __restrict__ geom, in
     t.mode = (xmin >= ulo + m && xmax <= uhi - m && ymin >= vlo + m && ymax <= vhi - m)
                  ? MODE_INTERIOR
                  : MODE_EDGE;
+    // central differences at the tap pixels use interior neighbours only:
+    // taps in [1, n-2], i.e. floor in [1, n-3]
+    t.csafe = xmin >= ulo + 1.0f + m && xmax <= uhi - 1.0f - m && ymin >= vlo + 1.0f + m &&
+              ymax <= vhi - 1.0f - m;
     const int u0 = max((int)floorf(xmin - m) + au, 0), u1 = min((int)floorf(xmax + m) + 1 + au, nu - 1);
     const int v0 = max((int)floorf(ymin - m) + av, 0), v1 = min((int)floorf(ymax + m) + 1 + av, nv - 1);
     if (u1 >= u0 && v1 >= v0) {
@@ -380,7 +384,7 @@ __global__ void __launch_bounds__(NT, FWD_MINB)
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   T* bufs = reinterpret_cast<T*>(dyn_smem);
   constexpr int CAP = STAGE_BYTES / (int)sizeof(T);
-  const TileIdx ti = tile_index<ZB>(vi);
+  const TileIdx ti = tile_index<ZB>(vi, blockIdx.x);
   float acc[ZB];
 #pragma unroll
   for (int k = 0; k < ZB; ++k) acc[k] = 0.0f;
@@ -624,11 +628,21 @@ __device__ __forceinline__ int scatter_slot(int lane) {
 // derivative of omega = wgt r^2 adds -2 s r val to the w component.  The
 // 3x4 outer product with (dq, 1) is accumulated as S_r = sum a_r and
 // Z_r = sum a_r dz along the thread's column; dx, dy are constant per thread.
-template <int ZB, typename T, bool FDK, bool EXACT, bool EDGE, bool PROJ>
-__device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, float* pout,
-                                         long long rs, int nu, int nv, const TileView& t, float dx,
-                                         float dy, const float (&delta)[ZB], float (&S)[3],
-                                         float (&Z)[3]) {
+//
+// Sources of the samples (SRC):
+//   SRC_GLOBAL  gradient images (CENTRAL) or raw taps (EXACT) from global memory;
+//   SRC_SMEM    the tile footprint staged in shared memory -- raw taps for
+//               EXACT, and for CENTRAL the 4x4-minus-corners neighbourhood
+//               whose central differences equal the gradient images there
+//               (only for "central-safe" tiles, whose differences never use
+//               the one-sided edge rule).
+enum { SRC_GLOBAL = 0, SRC_SMEM = 1 };
+
+template <int ZB, typename T, bool FDK, bool EXACT, bool EDGE, bool PROJ, int SRC>
+__device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, const T* buf,
+                                         const Stage& st, float* pout, long long rs, int nu,
+                                         int nv, const TileView& t, float dx, float dy,
+                                         const float (&delta)[ZB], float (&S)[3], float (&Z)[3]) {
   float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
   float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
   float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
@@ -638,15 +652,31 @@ __device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, float
     Sample s = locate<EDGE>(fmaf(dz, t.ru[2], u0), fmaf(dz, t.rv[2], v0), fmaf(dz, t.rw[2], w0),
                             t, nu, nv);
     if (EDGE && !s.ok) continue;
-    float gu, gv, val = 0.0f;
+    float gu, gv, val = 0.0f, gscale = 1.0f;
     if (EXACT) {
       float d00, d10, d01, d11;
-      taps<EDGE>(img, rs, nu, nv, s, d00, d10, d01, d11);
+      if (SRC == SRC_SMEM)
+        taps_smem<EDGE>(buf, st, nu, nv, s, d00, d10, d01, d11);
+      else
+        taps<EDGE>(img, rs, nu, nv, s, d00, d10, d01, d11);
       const float a = d10 - d00, b = d11 - d01;
       gu = fmaf(s.tv, b - a, a);
       const float c = d01 - d00, d = d11 - d10;
       gv = fmaf(s.tu, d - c, c);
       if (FDK) val = bilerp(s.tu, s.tv, d00, d10, d01, d11);
+    } else if (SRC == SRC_SMEM) {
+      // central-safe interior tile: 12 staged taps around (iu, iv)
+      const int p = st.pitch;
+      const T* q = buf + (s.iv - st.v0) * p + (s.iu - st.x0);
+      const float a0 = tof(q[-p]), a1 = tof(q[-p + 1]);
+      const float b0 = tof(q[-1]), b1 = tof(q[0]), b2 = tof(q[1]), b3 = tof(q[2]);
+      const float c0 = tof(q[p - 1]), c1 = tof(q[p]), c2 = tof(q[p + 1]), c3 = tof(q[p + 2]);
+      const float e0 = tof(q[2 * p]), e1 = tof(q[2 * p + 1]);
+      // twice the central-difference gradient images at the four tap pixels
+      gu = bilerp(s.tu, s.tv, b2 - b0, b3 - b1, c2 - c0, c3 - c1);
+      gv = bilerp(s.tu, s.tv, c1 - a0, c2 - a1, e0 - b1, e1 - b2);
+      gscale = 0.5f;
+      if (FDK) val = bilerp(s.tu, s.tv, b1, b2, c1, c2);
     } else {
       float2 g00, g10, g01, g11;
       const float2 z2 = make_float2(0.0f, 0.0f);
@@ -675,7 +705,8 @@ __device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, float
     }
     float sd = delta[k] * (FDK ? s.rwi * (s.rwi * t.wgt) : t.wgt);
     const float sr = sd * s.rwi;
-    const float a0 = gu * sr, a1 = gv * sr;
+    const float sg = sr * gscale;
+    const float a0 = gu * sg, a1 = gv * sg;
     float a2 = -fmaf(a0, s.x, a1 * s.y);
     if (FDK) a2 = fmaf(-2.0f * sr, val, a2);
     S[0] += a0;
@@ -689,16 +720,87 @@ __device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, float
   }
 }
 
+// One view of one tile: the sample loop (from the staged footprint when it
+// was staged), then the warp reduce-scatter of the 12 sums into red[][b].
 template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ>
+__device__ __forceinline__ void vjp_tile_view(const T* img, const float2* gimg, const T* buf,
+                                              const Stage& st, float* pout, const ProjInfo& pi,
+                                              const TileView& t, const TileIdx& ti,
+                                              const float (&delta)[ZB],
+                                              float (*red)[VB][12], int b) {
+  float S[3] = {0.0f, 0.0f, 0.0f}, Z[3] = {0.0f, 0.0f, 0.0f};
+  const bool smem = st.on && (EXACT || t.csafe);
+  if (smem) {
+    if (t.mode == MODE_INTERIOR)
+      vjp_view<ZB, T, FDK, EXACT, false, PROJ, SRC_SMEM>(img, gimg, buf, st, pout, pi.rs, pi.nu,
+                                                         pi.nv, t, ti.dx, ti.dy, delta, S, Z);
+    else
+      vjp_view<ZB, T, FDK, EXACT, true, PROJ, SRC_SMEM>(img, gimg, buf, st, pout, pi.rs, pi.nu,
+                                                        pi.nv, t, ti.dx, ti.dy, delta, S, Z);
+  } else {
+    if (t.mode == MODE_INTERIOR)
+      vjp_view<ZB, T, FDK, EXACT, false, PROJ, SRC_GLOBAL>(img, gimg, buf, st, pout, pi.rs, pi.nu,
+                                                           pi.nv, t, ti.dx, ti.dy, delta, S, Z);
+    else
+      vjp_view<ZB, T, FDK, EXACT, true, PROJ, SRC_GLOBAL>(img, gimg, buf, st, pout, pi.rs, pi.nu,
+                                                          pi.nv, t, ti.dx, ti.dy, delta, S, Z);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float v[16];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    v[4 * r + 0] = ti.dx * S[r];
+    v[4 * r + 1] = ti.dy * S[r];
+    v[4 * r + 2] = Z[r];
+    v[4 * r + 3] = S[r];
+  }
+  v[12] = v[13] = v[14] = v[15] = 0.0f;
+  const float tot = warp_reduce_scatter16(v, lane);
+  const int slot = scatter_slot(lane);
+  if (!(lane & 1) && slot < 12) red[warp][b][slot] = tot;
+}
+
+// Write the records of one batch of views: fixed-order sum of the 8 warps'
+// values, plus the anchors.
+__device__ __forceinline__ void vjp_flush_batch(const TileView* tv, float (*red)[VB][12], int j0,
+                                                int nb, bool any, int tile, int ntiles,
+                                                float* __restrict__ partials) {
+  for (int e = threadIdx.x; e < nb * PSLOTS; e += NT) {
+    const int b = e / PSLOTS, slot = e % PSLOTS;
+    float val = 0.0f;
+    if (slot < 12) {
+      if (any && tv[b].mode != MODE_SKIP)
+        for (int w = 0; w < NT / 32; ++w) val += red[w][b][slot];
+    } else if (slot == 12) {
+      val = (float)tv[b].au;
+    } else if (slot == 13) {
+      val = (float)tv[b].av;
+    }
+    partials[((long long)(j0 + b) * ntiles + tile) * PSLOTS + slot] = val;
+  }
+}
+
+// Motion VJP (optionally fused with the data VJP).  Grid: (view chunk, tile),
+// tiles fastest, so the CTAs resident at any time share a few views whose
+// data and dL/dproj rows stay in L2.  Per tile the views of the chunk are
+// processed in order with the footprint of view j+1 copied to shared memory
+// while view j is computed (STAGE), like the forward.
+template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ, bool STAGE>
 __global__ void __launch_bounds__(NT, VJP_MINB)
     vjp_motion_kernel(const float* __restrict__ dvol, const T* __restrict__ proj, ProjInfo pi,
                       const float2* __restrict__ grad, const ViewGeom* __restrict__ geom,
-                      VolInfo vi, float* __restrict__ partials, float* __restrict__ dproj) {
-  __shared__ TileView tvs[VB];
+                      VolInfo vi, float* __restrict__ partials, float* __restrict__ dproj,
+                      int vchunk) {
+  __shared__ TileView tvs[2][VB];
   __shared__ float red[NT / 32][VB][12];
-  const TileIdx ti = tile_index<ZB>(vi);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* bufs = reinterpret_cast<T*>(dyn_smem);
+  constexpr int CAP = STAGE_BYTES / (int)sizeof(T);
+  constexpr int HALO = EXACT ? 0 : 1;
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
+  const int tile = blockIdx.x % ntiles;
+  const int vbeg = (blockIdx.x / ntiles) * vchunk, vend = min(pi.nviews, vbeg + vchunk);
+  const TileIdx ti = tile_index<ZB>(vi, tile);
   const int i = ti.tx * TX + ti.lx, j = ti.ty * TY + ti.ly;
   float delta[ZB];
   bool nz = false;
@@ -711,80 +813,133 @@ __global__ void __launch_bounds__(NT, VJP_MINB)
     nz |= delta[k] != 0.0f;
   }
   const bool any = __syncthreads_or(nz);
-  for (int j0 = 0; j0 < pi.nviews; j0 += VB) {
-    const int nb = min(VB, pi.nviews - j0);
+  const int nvw = vend - vbeg, nbatch = (nvw + VB - 1) / VB;
+  setup_batch(tvs[0], geom, vbeg, min(VB, nvw), ti, pi.nu, pi.nv, true);
+  if (nbatch > 1) setup_batch(tvs[1], geom, vbeg + VB, min(VB, nvw - VB), ti, pi.nu, pi.nv, true);
+  __syncthreads();
+  auto plan = [&](const TileView& tv) {
+    Stage st = Stage{0, 0, 0, 0, 0, false};
+    if (STAGE && any && (EXACT || tv.csafe)) st = stage_plan<T>(tv, HALO, pi.nu, pi.nv);
+    return st;
+  };
+  Stage st_cur = plan(tvs[0][0]);
+  if (st_cur.on) stage_issue(bufs, proj + (long long)vbeg * pi.vs, pi.rs, st_cur);
+  cp_async_commit();
+  for (int v = vbeg; v < vend; ++v) {
+    const int idx = v - vbeg, k = idx / VB, b = idx - k * VB;
+    if (b == 0 && k >= 1) {
+      // batch k-1 is complete: write its records, then reuse its slot
+      vjp_flush_batch(tvs[(k - 1) & 1], red, vbeg + (k - 1) * VB, VB, any, tile, ntiles,
+                      partials);
+      __syncthreads();
+      if (k + 1 < nbatch)
+        setup_batch(tvs[(k + 1) & 1], geom, vbeg + (k + 1) * VB, min(VB, nvw - (k + 1) * VB), ti,
+                    pi.nu, pi.nv, true);
+      __syncthreads();
+    }
+    const TileView t = tvs[k & 1][b];
+    Stage st_next = Stage{0, 0, 0, 0, 0, false};
+    if (STAGE && v + 1 < vend) {
+      const int kn = (idx + 1) / VB;
+      st_next = plan(tvs[kn & 1][idx + 1 - kn * VB]);
+      if (st_next.on)
+        stage_issue(bufs + ((idx + 1) & 1) * CAP, proj + (long long)(v + 1) * pi.vs, pi.rs,
+                    st_next);
+    }
+    cp_async_commit();
+    cp_async_wait1();
     __syncthreads();
-    setup_batch(tvs, geom, j0, nb, ti, pi.nu, pi.nv, true);
-    __syncthreads();
-    if (any) {
-      for (int b = 0; b < nb; ++b) {
-        const TileView t = tvs[b];
-        if (t.mode == MODE_SKIP) continue;
-        const T* img = proj + (long long)(j0 + b) * pi.vs;
-        const float2* gimg = EXACT ? nullptr : grad + (long long)(j0 + b) * pi.nv * pi.nu;
-        float S[3] = {0.0f, 0.0f, 0.0f}, Z[3] = {0.0f, 0.0f, 0.0f};
-        float* pout = PROJ ? dproj + (long long)(j0 + b) * pi.nv * pi.nu : nullptr;
-        if (t.mode == MODE_INTERIOR)
-          vjp_view<ZB, T, FDK, EXACT, false, PROJ>(img, gimg, pout, pi.rs, pi.nu, pi.nv, t, ti.dx,
-                                                   ti.dy, delta, S, Z);
-        else
-          vjp_view<ZB, T, FDK, EXACT, true, PROJ>(img, gimg, pout, pi.rs, pi.nu, pi.nv, t, ti.dx,
-                                                  ti.dy, delta, S, Z);
-        float v[16];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          v[4 * r + 0] = ti.dx * S[r];
-          v[4 * r + 1] = ti.dy * S[r];
-          v[4 * r + 2] = Z[r];
-          v[4 * r + 3] = S[r];
-        }
-        v[12] = v[13] = v[14] = v[15] = 0.0f;
-        const float tot = warp_reduce_scatter16(v, lane);
-        const int slot = scatter_slot(lane);
-        if (!(lane & 1) && slot < 12) red[warp][b][slot] = tot;
-      }
+    if (any && t.mode != MODE_SKIP) {
+      const T* img = proj + (long long)v * pi.vs;
+      const float2* gimg = EXACT ? nullptr : grad + (long long)v * pi.nv * pi.nu;
+      float* pout = PROJ ? dproj + (long long)v * pi.nv * pi.nu : nullptr;
+      vjp_tile_view<ZB, T, FDK, EXACT, PROJ>(img, gimg, bufs + (idx & 1) * CAP, st_cur, pout, pi,
+                                             t, ti, delta, red, b);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < nb * PSLOTS; e += NT) {
-      const int b = e / PSLOTS, slot = e % PSLOTS;
-      float val = 0.0f;
-      if (slot < 12) {
-        if (any && tvs[b].mode != MODE_SKIP)
-          for (int w = 0; w < NT / 32; ++w) val += red[w][b][slot];
-      } else if (slot == 12) {
-        val = (float)tvs[b].au;
-      } else if (slot == 13) {
-        val = (float)tvs[b].av;
-      }
-      partials[((long long)(j0 + b) * ntiles + blockIdx.x) * PSLOTS + slot] = val;
-    }
+    st_cur = st_next;
   }
+  if (nvw > 0) {
+    const int kl = (nvw - 1) / VB;
+    vjp_flush_batch(tvs[kl & 1], red, vbeg + kl * VB, nvw - kl * VB, any, tile, ntiles, partials);
+  }
+}
+
+// Views per chunk of the view-chunked VJP grids: keep the bytes that one
+// chunk's views touch (projections, gradient images, dL/dproj rows) near
+// 64 MiB, well inside the 126 MiB L2.
+static int view_chunk(const ProjInfo& pi, long long bytes_per_px) {
+  const long long per_view = (long long)pi.nu * pi.nv * bytes_per_px;
+  long long c = (64LL << 20) / (per_view > 0 ? per_view : 1);
+  if (c < 1) c = 1;
+  if (c > VB) c = VB;
+  return (int)c;
+}
+
+template <typename T, bool FDK, bool EXACT, bool PROJ, bool STAGE>
+static cudaError_t vjp_launch(const float* dvol, const void* proj, const ProjInfo& pi,
+                              const float2* grad, const ViewGeom* geom, const VolInfo& vi,
+                              float* partials, float* dproj, int vc, unsigned nblocks,
+                              cudaStream_t s) {
+  const int smem = STAGE ? 2 * STAGE_BYTES : 0;
+  if (STAGE) {
+    cudaError_t e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, FDK, EXACT, PROJ, STAGE>>(smem);
+    if (e != cudaSuccess) return e;
+  }
+  vjp_motion_kernel<ZB_VJP, T, FDK, EXACT, PROJ, STAGE><<<nblocks, NT, smem, s>>>(
+      dvol, (const T*)proj, pi, grad, geom, vi, partials, dproj, vc);
+  return cudaGetLastError();
 }
 
 template <typename T, bool FDK, bool EXACT>
-static void vjp_dispatch(const float* dvol, const void* proj, const ProjInfo& pi,
-                         const float2* grad, const ViewGeom* geom, const VolInfo& vi,
-                         float* partials, float* dproj, cudaStream_t s) {
+static cudaError_t vjp_dispatch(const float* dvol, const void* proj, const ProjInfo& pi,
+                                const float2* grad, const ViewGeom* geom, const VolInfo& vi,
+                                float* partials, float* dproj, cudaStream_t s) {
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
+  const long long bpp = (long long)sizeof(T) + (EXACT ? 0 : 8) + (dproj ? 4 : 0);
+  const int vc = view_chunk(pi, bpp);
+  const unsigned nblocks = (unsigned)((long long)ntiles * ((pi.nviews + vc - 1) / vc));
+  const bool stage = stageable<T>(proj, pi);
   if (dproj)
-    vjp_motion_kernel<ZB_VJP, T, FDK, EXACT, true>
-        <<<ntiles, NT, 0, s>>>(dvol, (const T*)proj, pi, grad, geom, vi, partials, dproj);
-  else
-    vjp_motion_kernel<ZB_VJP, T, FDK, EXACT, false>
-        <<<ntiles, NT, 0, s>>>(dvol, (const T*)proj, pi, grad, geom, vi, partials, nullptr);
+    return stage ? vjp_launch<T, FDK, EXACT, true, true>(dvol, proj, pi, grad, geom, vi, partials,
+                                                         dproj, vc, nblocks, s)
+                 : vjp_launch<T, FDK, EXACT, true, false>(dvol, proj, pi, grad, geom, vi,
+                                                          partials, dproj, vc, nblocks, s);
+  return stage ? vjp_launch<T, FDK, EXACT, false, true>(dvol, proj, pi, grad, geom, vi, partials,
+                                                        nullptr, vc, nblocks, s)
+               : vjp_launch<T, FDK, EXACT, false, false>(dvol, proj, pi, grad, geom, vi,
+                                                         partials, nullptr, vc, nblocks, s);
+}
+
+// Set the VJP kernels' shared-memory attributes on the current device
+// (call before capturing a graph).
+cudaError_t prepare_vjp(int dtype, int fdk, int exact) {
+  const int smem = 2 * STAGE_BYTES;
+  cudaError_t e = cudaSuccess;
+#define BP_PREP(T)                                                                                 \
+  do {                                                                                             \
+    if (fdk && exact) e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, true, true, false, true>>(smem); \
+    if (fdk && !exact) e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, true, false, false, true>>(smem); \
+    if (!fdk && exact) e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, false, true, false, true>>(smem); \
+    if (!fdk && !exact) e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, false, false, false, true>>(smem); \
+  } while (0)
+  if (dtype == 0) BP_PREP(float);
+  else if (dtype == 1) BP_PREP(__half);
+  else BP_PREP(__nv_bfloat16);
+#undef BP_PREP
+  return e;
 }
 
 template <typename T>
-static void vjp_dispatch_t(int fdk, int exact, const float* dvol, const void* proj,
-                           const ProjInfo& pi, const float2* grad, const ViewGeom* geom,
-                           const VolInfo& vi, float* partials, float* dproj, cudaStream_t s) {
-  if (fdk) {
-    exact ? vjp_dispatch<T, true, true>(dvol, proj, pi, grad, geom, vi, partials, dproj, s)
-          : vjp_dispatch<T, true, false>(dvol, proj, pi, grad, geom, vi, partials, dproj, s);
-  } else {
-    exact ? vjp_dispatch<T, false, true>(dvol, proj, pi, grad, geom, vi, partials, dproj, s)
-          : vjp_dispatch<T, false, false>(dvol, proj, pi, grad, geom, vi, partials, dproj, s);
-  }
+static cudaError_t vjp_dispatch_t(int fdk, int exact, const float* dvol, const void* proj,
+                                  const ProjInfo& pi, const float2* grad, const ViewGeom* geom,
+                                  const VolInfo& vi, float* partials, float* dproj,
+                                  cudaStream_t s) {
+  if (fdk)
+    return exact ? vjp_dispatch<T, true, true>(dvol, proj, pi, grad, geom, vi, partials, dproj, s)
+                 : vjp_dispatch<T, true, false>(dvol, proj, pi, grad, geom, vi, partials, dproj, s);
+  return exact ? vjp_dispatch<T, false, true>(dvol, proj, pi, grad, geom, vi, partials, dproj, s)
+               : vjp_dispatch<T, false, false>(dvol, proj, pi, grad, geom, vi, partials, dproj, s);
 }
 
 cudaError_t launch_vjp_motion(const float* dvol, const void* proj, int dtype, const ProjInfo& pi,
@@ -792,12 +947,11 @@ cudaError_t launch_vjp_motion(const float* dvol, const void* proj, int dtype, co
                               int fdk, int exact, float* partials, float* dproj, cudaStream_t s) {
   if (vi.zb != ZB_VJP) return cudaErrorInvalidValue;
   if (dtype == 0)
-    vjp_dispatch_t<float>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, dproj, s);
-  else if (dtype == 1)
-    vjp_dispatch_t<__half>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, dproj, s);
-  else
-    vjp_dispatch_t<__nv_bfloat16>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, dproj, s);
-  return cudaGetLastError();
+    return vjp_dispatch_t<float>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, dproj, s);
+  if (dtype == 1)
+    return vjp_dispatch_t<__half>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, dproj, s);
+  return vjp_dispatch_t<__nv_bfloat16>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials,
+                                       dproj, s);
 }
 
 // ------------------------------------------------- VJP w.r.t. the data
@@ -829,9 +983,12 @@ __device__ __forceinline__ void proj_view(float* out, int nu, int nv, const Tile
 template <int ZB, bool FDK>
 __global__ void __launch_bounds__(NT, 2)
     vjp_proj_kernel(const float* __restrict__ dvol, ProjInfo pi, const ViewGeom* __restrict__ geom,
-                    VolInfo vi, float* __restrict__ dproj) {
+                    VolInfo vi, float* __restrict__ dproj, int vchunk) {
   __shared__ TileView tvs[VB];
-  const TileIdx ti = tile_index<ZB>(vi);
+  const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
+  const int tile = blockIdx.x % ntiles;
+  const int vbeg = (blockIdx.x / ntiles) * vchunk, vend = min(pi.nviews, vbeg + vchunk);
+  const TileIdx ti = tile_index<ZB>(vi, tile);
   const int i = ti.tx * TX + ti.lx, j = ti.ty * TY + ti.ly;
   float delta[ZB];
   bool nz = false;
@@ -844,8 +1001,8 @@ __global__ void __launch_bounds__(NT, 2)
     nz |= delta[k] != 0.0f;
   }
   if (!__syncthreads_or(nz)) return;
-  for (int j0 = 0; j0 < pi.nviews; j0 += VB) {
-    const int nb = min(VB, pi.nviews - j0);
+  for (int j0 = vbeg; j0 < vend; j0 += VB) {
+    const int nb = min(VB, vend - j0);
     __syncthreads();
     setup_batch(tvs, geom, j0, nb, ti, pi.nu, pi.nv, true);
     __syncthreads();
@@ -865,10 +1022,12 @@ cudaError_t launch_vjp_proj(const float* dvol, const ProjInfo& pi, const ViewGeo
                             const VolInfo& vi, int fdk, float* dproj, cudaStream_t s) {
   if (vi.zb != ZB_VJP) return cudaErrorInvalidValue;
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
+  const int vc = view_chunk(pi, 4);
+  const unsigned nblocks = (unsigned)((long long)ntiles * ((pi.nviews + vc - 1) / vc));
   if (fdk)
-    vjp_proj_kernel<ZB_VJP, true><<<ntiles, NT, 0, s>>>(dvol, pi, geom, vi, dproj);
+    vjp_proj_kernel<ZB_VJP, true><<<nblocks, NT, 0, s>>>(dvol, pi, geom, vi, dproj, vc);
   else
-    vjp_proj_kernel<ZB_VJP, false><<<ntiles, NT, 0, s>>>(dvol, pi, geom, vi, dproj);
+    vjp_proj_kernel<ZB_VJP, false><<<nblocks, NT, 0, s>>>(dvol, pi, geom, vi, dproj, vc);
   return cudaGetLastError();
 }
 
