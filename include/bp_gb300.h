@@ -159,6 +159,14 @@ int bp_vjp(bp_ctx* ctx, const float* dL_dvol, const void* proj, const bp_proj_de
 int bp_sharpness(bp_ctx* ctx, const float* vol, const bp_vol_desc* vdesc, double* loss,
                  float* dL_dvol, void* stream);
 
+/* Smoothed isotropic total variation of a volume, the classical autofocus
+ * metric the paper compares against (Sec. IV-A, "TV"):
+ *   L = (1/K) sum over voxels x with all three forward neighbours inside of
+ *       sqrt(|grad+ I(x)|^2 + eps^2),  grad+ = forward differences, K = nx*ny*nz;
+ * loss float64 (host or device), dL_dvol float32 (may be NULL), eps > 0. */
+int bp_tv(bp_ctx* ctx, const float* vol, const bp_vol_desc* vdesc, double eps, double* loss,
+          float* dL_dvol, void* stream);
+
 /* Allocation-free sharpness loss.  The paper has no counterpart: this is for
  * callers that cannot allocate device memory during the call -- code being
  * recorded into a CUDA graph (an allocation would break the stream capture),
@@ -203,6 +211,7 @@ int bp_adam_step(bp_ctx* ctx, int nviews, double* theta, const double* grad, dou
  * (Eq. 6 or Adam), followed by the view-mean gauge step. */
 
 typedef enum { BP_OPT_GD = 0 /* Eq. 6 */, BP_OPT_ADAM = 1 } bp_optimizer;
+typedef enum { BP_LOSS_SHARPNESS = 0 /* bp_sharpness */, BP_LOSS_TV = 1 /* bp_tv */ } bp_loss;
 
 typedef struct {
   int optimizer;    /* bp_optimizer */
@@ -211,6 +220,8 @@ typedef struct {
   double decay;     /* Eq. 6 t (GD only) */
   double beta1, beta2, eps;  /* Adam */
   int gauge;        /* remove the per-parameter view mean after each step */
+  int loss;         /* bp_loss: the image-quality target minimised */
+  double tv_eps;    /* eps of BP_LOSS_TV */
 } bp_opt_desc;
 
 typedef struct bp_job bp_job;
@@ -230,16 +241,20 @@ long long bp_job_bytes_for(const bp_proj_desc* pdesc, const bp_vol_desc* vdesc, 
                            int max_iters);
 long long bp_job_bytes(const bp_job* job);
 int bp_ctx_set_hbm_budget(bp_ctx* ctx, long long bytes);
-/* Run n_iters iterations on `stream` (asynchronous).  The first call
- * captures the iteration graph on a job-owned stream. */
+/* Run n_iters iterations on `stream` (asynchronous; the replays wait for
+ * the job's earlier work).  The first call captures the iteration graph on a
+ * job-owned stream.  Jobs on different streams overlap on the device. */
 int motion_step(bp_job* job, int n_iters, void* stream);
-/* Synchronise the device and copy theta (float64 [V][6]) and the loss
- * history (float64 [max_iters], may be NULL) to host memory; *iters_done
- * (may be NULL) receives the number of iterations run. */
+/* Wait for the job's queued iterations (not for other work on the device)
+ * and copy theta (float64 [V][6]) and the loss history (float64
+ * [max_iters], may be NULL) to host memory; *iters_done (may be NULL)
+ * receives the number of iterations run. */
 int bp_job_get_motion(const bp_job* job, double* theta_host, double* loss_history,
                       int* iters_done);
 /* The job's current volume (float32, device pointer owned by the job). */
 const float* bp_job_volume(const bp_job* job);
+/* Waits for the job's queued iterations, then frees its memory with the
+ * stream-ordered allocator (no device-wide synchronisation). */
 void bp_job_destroy(bp_job* job);
 
 #ifdef __cplusplus

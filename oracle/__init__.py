@@ -1,7 +1,7 @@
 """Oracle: plain FP64 CPU restatement of the paper's backprojection (Eq. 3),
 its analytic Jacobian (Eqs. 4-5), the rigid motion composition (Eq. 1), the
 chain rule (Eq. 2), the gradient-descent update (Eq. 6), Adam, a sharpness
-loss and the reprojection error (Sec. IV-A).
+loss, total variation and the reprojection error (Sec. IV-A).
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package; the product path
@@ -56,6 +56,8 @@ def _load():
         lib.orc_chain_motion.argtypes = [ctypes.c_int, dp, dp, dp, dp]
         lib.orc_sharpness.argtypes = [ctypes.POINTER(_Vol), dp, dp]
         lib.orc_sharpness.restype = ctypes.c_double
+        lib.orc_tv.argtypes = [ctypes.POINTER(_Vol), dp, ctypes.c_double, dp]
+        lib.orc_tv.restype = ctypes.c_double
         lib.orc_gd_step.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int, ctypes.c_int]
         lib.orc_adam_step.argtypes = [ctypes.c_int, dp, dp, dp, dp, ctypes.c_double,
@@ -173,6 +175,16 @@ def sharpness(vol, spacing=(1, 1, 1), origin=(0, 0, 0), want_grad=True):
     g = _vol(vol.shape, spacing, origin)
     grad = np.zeros_like(vol) if want_grad else None
     L = _load().orc_sharpness(ctypes.byref(g), _ptr(vol), _ptr(grad))
+    return float(L), grad
+
+
+def tv(vol, eps, want_grad=True):
+    """Smoothed isotropic total variation L = (1/K) sum sqrt(|grad+ I|^2 + eps^2)
+    over voxels with all forward neighbours inside; (L, dL/dI)."""
+    vol = _f64(vol)
+    g = _vol(vol.shape, (1, 1, 1), (0, 0, 0))
+    grad = np.zeros_like(vol) if want_grad else None
+    L = _load().orc_tv(ctypes.byref(g), _ptr(vol), float(eps), _ptr(grad))
     return float(L), grad
 
 

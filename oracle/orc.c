@@ -356,6 +356,35 @@ double orc_sharpness(const orc_vol* g, const double* vol, double* grad) {
   return L;
 }
 
+/* Total variation (isotropic, smoothed), the classical autofocus metric the
+ * paper compares against (Sec. IV-A):
+ *   L = (1/K) sum over voxels x with all three forward neighbours inside of
+ *       sqrt(|grad+ I(x)|^2 + eps^2),  grad+ = forward differences,
+ * K = nx*ny*nz; grad receives dL/dI.  Returns L. */
+double orc_tv(const orc_vol* g, const double* vol, double eps, double* grad) {
+  const long nx = g->nx, ny = g->ny, nz = g->nz;
+  const double K = (double)nx * ny * nz;
+  double L = 0.0;
+  if (grad) memset(grad, 0, sizeof(double) * nx * ny * nz);
+  for (long k = 0; k + 1 < nz; ++k)
+    for (long j = 0; j + 1 < ny; ++j)
+      for (long i = 0; i + 1 < nx; ++i) {
+        size_t x = ((size_t)k * ny + j) * nx + i;
+        double gx = vol[x + 1] - vol[x];
+        double gy = vol[x + nx] - vol[x];
+        double gz = vol[x + (size_t)nx * ny] - vol[x];
+        double n = sqrt(gx * gx + gy * gy + gz * gz + eps * eps);
+        L += n / K;
+        if (grad) {
+          grad[x + 1] += gx / n / K;
+          grad[x + nx] += gy / n / K;
+          grad[x + (size_t)nx * ny] += gz / n / K;
+          grad[x] -= (gx + gy + gz) / n / K;
+        }
+      }
+  return L;
+}
+
 /* Remove the per-parameter mean over views (gauge of a global rigid motion). */
 static void remove_mean(int V, double* theta) {
   for (int m = 0; m < 6; ++m) {

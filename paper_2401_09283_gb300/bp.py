@@ -101,6 +101,19 @@ def bp_sharpness(vol, want_grad=True, loss_out=None, grad_out=None):
     return loss, grad
 
 
+def bp_tv(vol, eps=1e-3, want_grad=True, loss_out=None, grad_out=None):
+    """Smoothed isotropic total variation and dL/dvol; returns (loss, grad | None)."""
+    dev = vol.device if isinstance(vol, torch.Tensor) else torch.device("cpu")
+    loss = loss_out if loss_out is not None else torch.empty((), dtype=torch.float64, device=dev)
+    grad = grad_out if grad_out is not None else (torch.empty_like(vol) if want_grad else None)
+    vd = N.vol_desc(vol.shape, (1, 1, 1), (0, 0, 0))
+    ctx = N.context(N.device_of(vol))
+    rc = N.lib().bp_tv(ctx, N.ptr(vol), ctypes.byref(vd), float(eps), N.ptr(loss), N.ptr(grad),
+                       N.stream_of(vol))
+    N.check("bp_tv", rc, ctx)
+    return loss, grad
+
+
 def bp_gd_step(theta, grad, s0, t, n, gauge=True):
     """Eq. 6 step n in place on theta (V,6) float64."""
     ctx = N.context(N.device_of(theta))

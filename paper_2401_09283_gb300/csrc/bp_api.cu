@@ -370,6 +370,44 @@ int bp_sharpness(bp_ctx* ctx, const float* vol, const bp_vol_desc* vdesc, double
   return BP_OK;
 }
 
+int bp_tv(bp_ctx* ctx, const float* vol, const bp_vol_desc* vdesc, double eps, double* loss,
+          float* dL_dvol, void* stream) {
+  if (!ctx) return BP_ERR_INVALID_ARG;
+  ctx->err.clear();
+  int st = check_vol(ctx, vdesc);
+  if (st) return st;
+  const long long nvox = (long long)vdesc->nx * vdesc->ny * vdesc->nz;
+  if (!loss) return fail(ctx, BP_ERR_INVALID_ARG, "loss is NULL");
+  if (nvox > 0 && !vol) return fail(ctx, BP_ERR_INVALID_ARG, "vol is NULL");
+  if (!(eps > 0.0)) return fail(ctx, BP_ERR_INVALID_ARG, "eps must be > 0");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nvox == 0) {
+    if (is_host(loss)) {
+      *loss = 0.0;
+      return BP_OK;
+    }
+    CK(cudaMemsetAsync(loss, 0, sizeof(double), s), "zero loss");
+    return BP_OK;
+  }
+  const void* q;
+  CK(stage_in(ctx->s_vol, vol, sizeof(float) * nvox, s, &q), "copy vol");
+  void *ol, *og;
+  bool hl, hg;
+  CK(stage_out(ctx->s_loss, loss, sizeof(double), &ol, &hl), "alloc loss");
+  CK(stage_out(ctx->s_dvol, dL_dvol, sizeof(float) * nvox, &og, &hg), "alloc grad");
+  const int nb = bpk::sharpness_blocks(nvox);
+  CK(ensure(ctx->shblk, sizeof(double) * nb), "alloc block sums");
+  CK(TL(K_SHARPNESS, 2, bpk::launch_tv((const float*)q, vdesc->nx, vdesc->ny, vdesc->nz,
+                                       (float)eps, (double*)ctx->shblk.p, nb, (double*)ol,
+                                       nullptr, 0, (float*)og, s)),
+     "tv kernel");
+  if (hl) CK(cudaMemcpyAsync(loss, ol, sizeof(double), cudaMemcpyDeviceToHost, s), "copy loss");
+  if (hg) CK(cudaMemcpyAsync(dL_dvol, og, sizeof(float) * nvox, cudaMemcpyDeviceToHost, s), "copy grad");
+  if (hl || hg) CK(cudaStreamSynchronize(s), "sync");
+  return BP_OK;
+}
+
 }  // extern "C"
 
 namespace {

@@ -402,4 +402,105 @@ cudaError_t launch_gd_dev(int V, double* theta, const double* grad, double s0_t,
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ total variation
+
+// Smoothed isotropic TV, L = (1/K) sum over voxels x with all three forward
+// neighbours inside of n(x) = sqrt(|grad+ I(x)|^2 + eps^2).  Gather form of
+// the gradient: voxel y collects -(gx+gy+gz)/n from itself and g_a/n from
+// y - e_a for the axes whose neighbour is an interior voxel.
+__device__ __forceinline__ bool tv_interior(int i, int j, int k, int nx, int ny, int nz) {
+  return i >= 0 && j >= 0 && k >= 0 && i + 1 < nx && j + 1 < ny && k + 1 < nz;
+}
+
+__device__ __forceinline__ void tv_terms(const float* vol, long long x, long long nx,
+                                         long long nxy, float eps2, float& gx, float& gy,
+                                         float& gz, float& inv_n, double& n) {
+  const float c = vol[x];
+  gx = vol[x + 1] - c;
+  gy = vol[x + nx] - c;
+  gz = vol[x + nxy] - c;
+  n = sqrt((double)gx * gx + (double)gy * gy + (double)gz * gz + (double)eps2);
+  inv_n = (float)(1.0 / n);
+}
+
+template <bool HIST>
+__global__ void tv_kernel(const float* __restrict__ vol, int nx, int ny, int nz, float eps,
+                          double* __restrict__ block_sums, float* __restrict__ grad) {
+  __shared__ double red[SH_THREADS];
+  const long long nvox = (long long)nx * ny * nz;
+  const long long nxy = (long long)nx * ny;
+  const float invK = (float)(1.0 / (double)nvox);
+  const float eps2 = eps * eps;
+  double acc = 0.0;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < nvox;
+       x += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(x % nx), j = (int)((x / nx) % ny), k = (int)(x / nxy);
+    float gsum = 0.0f, gx, gy, gz, in;
+    double n;
+    if (tv_interior(i, j, k, nx, ny, nz)) {
+      tv_terms(vol, x, nx, nxy, eps2, gx, gy, gz, in, n);
+      acc += n;
+      gsum -= (gx + gy + gz) * in;
+    }
+    if (grad) {
+      if (tv_interior(i - 1, j, k, nx, ny, nz)) {
+        tv_terms(vol, x - 1, nx, nxy, eps2, gx, gy, gz, in, n);
+        gsum += gx * in;
+      }
+      if (tv_interior(i, j - 1, k, nx, ny, nz)) {
+        tv_terms(vol, x - nx, nx, nxy, eps2, gx, gy, gz, in, n);
+        gsum += gy * in;
+      }
+      if (tv_interior(i, j, k - 1, nx, ny, nz)) {
+        tv_terms(vol, x - nxy, nx, nxy, eps2, gx, gy, gz, in, n);
+        gsum += gz * in;
+      }
+      grad[x] = gsum * invK;
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = SH_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = red[0];
+}
+
+// loss = +sum/K (TV is minimised as is); with a history, at history[*iter].
+__global__ void tv_finish_kernel(const double* __restrict__ block_sums, int nb, double K,
+                                 double* __restrict__ loss, const int* __restrict__ iter,
+                                 int hist_len) {
+  __shared__ double red[SH_THREADS];
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += block_sums[b];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = SH_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (!iter) {
+      *loss = red[0] / K;
+    } else {
+      const int it = *iter;
+      if (it >= 0 && it < hist_len) loss[it] = red[0] / K;
+    }
+  }
+}
+
+cudaError_t launch_tv(const float* vol, int nx, int ny, int nz, float eps, double* block_sums,
+                      int max_blocks, double* loss, const int* iter, int hist_len, float* grad,
+                      cudaStream_t s) {
+  long long nvox = (long long)nx * ny * nz;
+  int nb = sharpness_blocks(nvox);
+  if (nb > max_blocks) nb = max_blocks;
+  tv_kernel<false><<<nb, SH_THREADS, 0, s>>>(vol, nx, ny, nz, eps, block_sums, grad);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  tv_finish_kernel<<<1, SH_THREADS, 0, s>>>(block_sums, nb, (double)nvox, loss, iter, hist_len);
+  return cudaGetLastError();
+}
+
 }  // namespace bpk

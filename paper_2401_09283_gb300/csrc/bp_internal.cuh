@@ -109,6 +109,12 @@ cudaError_t launch_adam(int V, double* theta, const double* grad, double* m1, do
 
 int sharpness_blocks(long long nvox);
 
+// Smoothed isotropic total variation and its gradient; iter == NULL writes
+// *loss, otherwise loss[*iter] (a history, graph-replayable).
+cudaError_t launch_tv(const float* vol, int nx, int ny, int nz, float eps, double* block_sums,
+                      int max_blocks, double* loss, const int* iter, int hist_len, float* grad,
+                      cudaStream_t s);
+
 // Graph-replayable variants: the iteration number lives on the device.
 cudaError_t launch_sharpness_hist(const float* vol, int nx, int ny, int nz, double* block_sums,
                                   int max_blocks, double* history, const int* iter, int hist_len,

@@ -26,6 +26,8 @@ struct bp_job {
   float *partials = nullptr, *vol = nullptr, *dvol = nullptr;
   int* iter = nullptr;
   long long bytes = 0;
+  cudaStream_t own = nullptr;   // the job's stream: allocation, copies, read-back
+  cudaEvent_t done = nullptr;   // recorded after the last queued iteration
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -66,15 +68,23 @@ Layout layout(const bp_proj_desc* pd, const bp_vol_desc* vd, int deriv, int max_
   return L;
 }
 
+// Free everything without a device-wide synchronisation: other jobs keep
+// running (stream-ordered free after the job's last queued iteration).
 void release(bp_job* j) {
+  if (j->own && j->done) cudaStreamWaitEvent(j->own, j->done, 0);
+  if (j->base) cudaFreeAsync(j->base, j->own);
+  if (j->own) cudaStreamSynchronize(j->own);
   if (j->exec) cudaGraphExecDestroy(j->exec);
   if (j->graph) cudaGraphDestroy(j->graph);
   if (j->cap) cudaStreamDestroy(j->cap);
-  if (j->base) cudaFree(j->base);
+  if (j->done) cudaEventDestroy(j->done);
+  if (j->own) cudaStreamDestroy(j->own);
   j->exec = nullptr;
   j->graph = nullptr;
   j->cap = nullptr;
   j->base = nullptr;
+  j->done = nullptr;
+  j->own = nullptr;
 }
 
 // Record one iteration on stream s.
@@ -87,8 +97,12 @@ cudaError_t record_iteration(bp_job* j, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   e = bpk::launch_forward(j->proj, j->pd.dtype, j->pi, j->geom, j->vi, fdk, j->vol, s);
   if (e != cudaSuccess) return e;
-  e = bpk::launch_sharpness_hist(j->vol, j->vd.nx, j->vd.ny, j->vd.nz, j->blk, j->nblk, j->hist,
-                                 j->iter, j->max_iters, j->dvol, s);
+  if (j->opt.loss == BP_LOSS_TV)
+    e = bpk::launch_tv(j->vol, j->vd.nx, j->vd.ny, j->vd.nz, (float)j->opt.tv_eps, j->blk, j->nblk,
+                       j->hist, j->iter, j->max_iters, j->dvol, s);
+  else
+    e = bpk::launch_sharpness_hist(j->vol, j->vd.nx, j->vd.ny, j->vd.nz, j->blk, j->nblk,
+                                   j->hist, j->iter, j->max_iters, j->dvol, s);
   if (e != cudaSuccess) return e;
   e = bpk::launch_vjp_motion(j->dvol, j->proj, j->pd.dtype, j->pi, j->grad, j->geom, j->vi, fdk,
                              j->deriv == BP_DERIV_BILINEAR_EXACT, j->partials, nullptr, s);
@@ -140,8 +154,10 @@ int bp_job_create(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, cons
     return fail(ctx, BP_ERR_INVALID_ARG, "bp_job_create: bad strides");
   if ((weight != BP_WEIGHT_NONE && weight != BP_WEIGHT_FDK) ||
       (deriv != BP_DERIV_CENTRAL && deriv != BP_DERIV_BILINEAR_EXACT) ||
-      (opt->optimizer != BP_OPT_GD && opt->optimizer != BP_OPT_ADAM))
-    return fail(ctx, BP_ERR_INVALID_ARG, "bp_job_create: unknown weight/deriv/optimizer");
+      (opt->optimizer != BP_OPT_GD && opt->optimizer != BP_OPT_ADAM) ||
+      (opt->loss != BP_LOSS_SHARPNESS && opt->loss != BP_LOSS_TV) ||
+      (opt->loss == BP_LOSS_TV && !(opt->tv_eps > 0.0)))
+    return fail(ctx, BP_ERR_INVALID_ARG, "bp_job_create: unknown weight/deriv/optimizer/loss");
   DeviceGuard g(ctx->device);
   const Layout L = layout(pdesc, vdesc, deriv, max_iters);
   // admission by device memory
@@ -167,11 +183,15 @@ int bp_job_create(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, cons
   j->deriv = deriv;
   j->max_iters = max_iters;
   j->bytes = L.total;
-  cudaError_t e = cudaMalloc(&j->base, (size_t)L.total);
+  cudaError_t e = cudaStreamCreateWithFlags(&j->own, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMallocAsync(&j->base, (size_t)L.total, j->own);
   if (e != cudaSuccess) {
+    release(j);
     delete j;
-    return cuda_fail(ctx, e, "bp_job_create: cudaMalloc");
+    return cuda_fail(ctx, e, "bp_job_create: allocation");
   }
+  cudaStream_t os = j->own;
   char* p = (char*)j->base;
   auto take = [&](long long n) {
     char* q = p;
@@ -197,29 +217,34 @@ int bp_job_create(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, cons
   const int V = pdesc->nviews;
   const size_t es = pdesc->dtype == BP_F32 ? 4 : 2;
   // inputs (host or device: cudaMemcpyDefault under unified addressing)
-  e = cudaMemcpy2D(j->proj, es * pdesc->nu, proj, es * pdesc->row_stride, es * pdesc->nu,
-                   (size_t)pdesc->nv, cudaMemcpyDefault);
-  for (int v = 1; v < V && e == cudaSuccess; ++v)
-    e = cudaMemcpy2D((char*)j->proj + es * (size_t)v * pdesc->nu * pdesc->nv, es * pdesc->nu,
-                     (const char*)proj + es * (size_t)v * pdesc->view_stride,
-                     es * pdesc->row_stride, es * pdesc->nu, (size_t)pdesc->nv, cudaMemcpyDefault);
-  if (e == cudaSuccess) e = cudaMemcpy(j->P, P, 96 * (size_t)V, cudaMemcpyDefault);
+  if (pdesc->view_stride == (long long)pdesc->nv * pdesc->row_stride) {
+    e = cudaMemcpy2DAsync(j->proj, es * pdesc->nu, proj, es * pdesc->row_stride, es * pdesc->nu,
+                          (size_t)pdesc->nv * V, cudaMemcpyDefault, os);
+  } else {
+    for (int v = 0; v < V && e == cudaSuccess; ++v)
+      e = cudaMemcpy2DAsync((char*)j->proj + es * (size_t)v * pdesc->nu * pdesc->nv,
+                            es * pdesc->nu, (const char*)proj + es * (size_t)v * pdesc->view_stride,
+                            es * pdesc->row_stride, es * pdesc->nu, (size_t)pdesc->nv,
+                            cudaMemcpyDefault, os);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(j->P, P, 96 * (size_t)V, cudaMemcpyDefault, os);
   if (e == cudaSuccess) {
-    if (view_weight) e = cudaMemcpy(j->vw, view_weight, 8 * (size_t)V, cudaMemcpyDefault);
+    if (view_weight) e = cudaMemcpyAsync(j->vw, view_weight, 8 * (size_t)V, cudaMemcpyDefault, os);
     else j->vw = nullptr;
   }
   if (e == cudaSuccess) {
-    if (pdesc->view_scale) e = cudaMemcpy(j->scale, pdesc->view_scale, 4 * (size_t)V, cudaMemcpyDefault);
+    if (pdesc->view_scale)
+      e = cudaMemcpyAsync(j->scale, pdesc->view_scale, 4 * (size_t)V, cudaMemcpyDefault, os);
     else j->scale = nullptr;
   }
   if (e == cudaSuccess) {
-    if (theta0) e = cudaMemcpy(j->theta, theta0, 48 * (size_t)V, cudaMemcpyDefault);
-    else e = cudaMemset(j->theta, 0, 48 * (size_t)V);
+    if (theta0) e = cudaMemcpyAsync(j->theta, theta0, 48 * (size_t)V, cudaMemcpyDefault, os);
+    else e = cudaMemsetAsync(j->theta, 0, 48 * (size_t)V, os);
   }
-  if (e == cudaSuccess) e = cudaMemset(j->m1, 0, 48 * (size_t)V);
-  if (e == cudaSuccess) e = cudaMemset(j->m2, 0, 48 * (size_t)V);
-  if (e == cudaSuccess) e = cudaMemset(j->iter, 0, sizeof(int));
-  if (e == cudaSuccess && max_iters > 0) e = cudaMemset(j->hist, 0, 8 * (size_t)max_iters);
+  if (e == cudaSuccess) e = cudaMemsetAsync(j->m1, 0, 48 * (size_t)V, os);
+  if (e == cudaSuccess) e = cudaMemsetAsync(j->m2, 0, 48 * (size_t)V, os);
+  if (e == cudaSuccess) e = cudaMemsetAsync(j->iter, 0, sizeof(int), os);
+  if (e == cudaSuccess && max_iters > 0) e = cudaMemsetAsync(j->hist, 0, 8 * (size_t)max_iters, os);
   j->pd.row_stride = pdesc->nu;
   j->pd.view_stride = (long long)pdesc->nu * pdesc->nv;
   j->pd.view_scale = j->scale;
@@ -247,13 +272,14 @@ int bp_job_create(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, cons
   j->ntiles = j->vi.tiles_x * j->vi.tiles_y * j->vi.tiles_z;
   j->nblk = bpk::sharpness_blocks((long long)vdesc->nx * vdesc->ny * vdesc->nz);
   if (e == cudaSuccess && j->grad) {
-    e = bpk::launch_grad_images(j->proj, pdesc->dtype, j->pi, j->grad, nullptr);
+    e = bpk::launch_grad_images(j->proj, pdesc->dtype, j->pi, j->grad, os);
     ctx->launches += 1;
   }
   if (e == cudaSuccess) e = bpk::prepare_forward(pdesc->dtype, weight == BP_WEIGHT_FDK);
   if (e == cudaSuccess)
     e = bpk::prepare_vjp(pdesc->dtype, weight == BP_WEIGHT_FDK, deriv == BP_DERIV_BILINEAR_EXACT);
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaEventRecord(j->done, os);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(os);
   if (e != cudaSuccess) {
     release(j);
     delete j;
@@ -286,11 +312,16 @@ int motion_step(bp_job* j, int n_iters, void* stream) {
     }
   }
   cudaStream_t s = (cudaStream_t)stream;
+  // the first replay waits for the job's set-up and any earlier read-back
+  cudaError_t e = cudaStreamWaitEvent(s, j->done, 0);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "motion_step: wait");
   for (int i = 0; i < n_iters; ++i) {
-    cudaError_t e = cudaGraphLaunch(j->exec, s);
+    e = cudaGraphLaunch(j->exec, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "motion_step: launch");
   }
   ctx->launches += (long long)kKernelsPerIteration * n_iters;
+  e = cudaEventRecord(j->done, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "motion_step: record");
   return BP_OK;
 }
 
@@ -298,12 +329,17 @@ int bp_job_get_motion(const bp_job* j, double* theta_host, double* loss_history,
                       int* iters_done) {
   if (!j) return BP_ERR_INVALID_ARG;
   DeviceGuard g(j->device);
-  cudaError_t e = cudaDeviceSynchronize();
+  // read back on the job's own stream after its last queued iteration; no
+  // device-wide synchronisation, so other jobs keep running
+  cudaStream_t os = j->own;
+  cudaError_t e = cudaStreamWaitEvent(os, j->done, 0);
   if (e == cudaSuccess && theta_host)
-    e = cudaMemcpy(theta_host, j->theta, 48 * (size_t)j->pd.nviews, cudaMemcpyDeviceToHost);
+    e = cudaMemcpyAsync(theta_host, j->theta, 48 * (size_t)j->pd.nviews, cudaMemcpyDeviceToHost, os);
   if (e == cudaSuccess && loss_history && j->max_iters > 0)
-    e = cudaMemcpy(loss_history, j->hist, 8 * (size_t)j->max_iters, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && iters_done) e = cudaMemcpy(iters_done, j->iter, sizeof(int), cudaMemcpyDeviceToHost);
+    e = cudaMemcpyAsync(loss_history, j->hist, 8 * (size_t)j->max_iters, cudaMemcpyDeviceToHost, os);
+  if (e == cudaSuccess && iters_done)
+    e = cudaMemcpyAsync(iters_done, j->iter, sizeof(int), cudaMemcpyDeviceToHost, os);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(os);
   if (e != cudaSuccess) return cuda_fail(j->ctx, e, "bp_job_get_motion");
   return BP_OK;
 }
@@ -313,7 +349,6 @@ const float* bp_job_volume(const bp_job* j) { return j ? j->vol : nullptr; }
 void bp_job_destroy(bp_job* j) {
   if (!j) return;
   DeviceGuard g(j->device);
-  cudaDeviceSynchronize();
   j->ctx->job_bytes -= j->bytes;
   release(j);
   delete j;

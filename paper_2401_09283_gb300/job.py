@@ -14,13 +14,14 @@ import torch
 from . import native as N
 
 OPT = {"gd": 0, "adam": 1}
+LOSS = {"sharpness": 0, "tv": 1}
 
 
 class MotionJob:
     def __init__(self, proj, P, *, vol_shape, spacing, origin, sid, view_weight=None,
                  weight="fdk", deriv="central", optimizer="adam", lr=0.1, lr_rot=1e-3,
                  decay=0.97, betas=(0.9, 0.999), eps=1e-8, gauge=True, theta0=None,
-                 max_iters=100, view_scale=None, device=None):
+                 max_iters=100, view_scale=None, device=None, loss="sharpness", tv_eps=1e-3):
         self.V = int(P.shape[0])
         self.max_iters = int(max_iters)
         if device is None:
@@ -30,7 +31,7 @@ class MotionJob:
         pd = N.proj_desc(proj, sid, view_scale)
         vd = N.vol_desc(vol_shape, spacing, origin)
         od = N.OptDesc(OPT[optimizer], float(lr), float(lr_rot), float(decay), float(betas[0]),
-                       float(betas[1]), float(eps), int(bool(gauge)))
+                       float(betas[1]), float(eps), int(bool(gauge)), LOSS[loss], float(tv_eps))
         Pc = P if isinstance(P, torch.Tensor) else torch.as_tensor(np.ascontiguousarray(P))
         self._keep = (proj, Pc, view_weight, theta0, view_scale)
         h = ctypes.c_void_p()

@@ -39,7 +39,8 @@ class ProjDesc(ctypes.Structure):
 
 class OptDesc(ctypes.Structure):
     _fields_ = [("optimizer", c_int), ("lr", c_double), ("lr_rot", c_double), ("decay", c_double),
-                ("beta1", c_double), ("beta2", c_double), ("eps", c_double), ("gauge", c_int)]
+                ("beta1", c_double), ("beta2", c_double), ("eps", c_double), ("gauge", c_int),
+                ("loss", c_int), ("tv_eps", c_double)]
 
 
 class BPError(RuntimeError):
@@ -54,7 +55,7 @@ _ctx = {}
 
 EXPORTS = ["bp_ctx_create", "bp_ctx_destroy", "bp_last_error", "bp_ctx_workspace_bytes",
            "bp_ctx_launch_count", "bp_ctx_set_timing", "bp_ctx_timing",
-           "bp_compose", "bp_forward", "bp_vjp", "bp_sharpness", "bp_sharpness_noalloc",
+           "bp_compose", "bp_forward", "bp_vjp", "bp_sharpness", "bp_tv", "bp_sharpness_noalloc",
            "bp_gd_step", "bp_adam_step", "bp_job_create", "bp_job_bytes_for", "bp_job_bytes",
            "bp_ctx_set_hbm_budget", "motion_step", "bp_job_get_motion", "bp_job_volume",
            "bp_job_destroy"]
@@ -91,6 +92,7 @@ def lib():
                 L.bp_vjp.argtypes = [vp, vp, vp, ctypes.POINTER(ProjDesc), vp, vp, vp, c_int,
                                      c_int, ctypes.POINTER(VolDesc), vp, vp, vp, vp]
                 L.bp_sharpness.argtypes = [vp, vp, ctypes.POINTER(VolDesc), vp, vp, vp]
+                L.bp_tv.argtypes = [vp, vp, ctypes.POINTER(VolDesc), c_double, vp, vp, vp]
                 L.bp_sharpness_noalloc.argtypes = [vp, ctypes.POINTER(VolDesc), vp, vp, vp]
                 L.bp_gd_step.argtypes = [vp, c_int, vp, vp, c_double, c_double, c_int, c_int, vp]
                 L.bp_adam_step.argtypes = [vp, c_int, vp, vp, vp, vp, c_double, c_double,

@@ -63,10 +63,16 @@ def test_gradcheck_motion_c4g():
 def test_fd_24_motion_parameters_c4():
     """Config 4 (192^3, 180 views, 320x240): the autograd gradient of
     L = <delta, vol> (FP32 kernels, exact bilinear derivative) on 24 seeded
-    parameters against central FD (h = 1e-3 mm / 1e-4 rad).  A view's
-    parameters change only that view's backprojection, so the FD is taken on
-    the FP64 oracle's single-view forward: FD of FP32 volumes would be
-    dominated by rounding (~6e-8 |I| sqrt(N) / 2h)."""
+    parameters against central finite differences.  A view's parameters
+    change only that view's backprojection, so the FD is taken on the FP64
+    oracle's single-view forward (FD of FP32 volumes is rounding-dominated).
+
+    Bilinear interpolation has kinks at pixel boundaries.  At the config's
+    h = 1e-3 mm / 1e-4 rad a voxel 128 mm off-axis moves 0.016 px per step,
+    so a few % of the voxel-views straddle a boundary and the FD is
+    kink-limited (measured median ~3e-2 on this phantom data); at
+    h = 1e-7 mm / 1e-9 rad, still well above FP64 rounding for a 7e6-term
+    sum, the FD converges to the derivative."""
     cfg, P, th, proj, delta, args = setup("c4")
     thg = th.clone().requires_grad_(True)
     vol = backproject(proj, thg, P, deriv="exact", **args)
@@ -78,27 +84,28 @@ def test_fd_24_motion_parameters_c4():
     vw = args["view_weight"].cpu().numpy()
     rng = np.random.default_rng(24)
     picks = [(int(rng.integers(cfg.views)), int(rng.integers(6))) for _ in range(24)]
-    rel = []
-    for j, m in picks:
-        h = 1e-3 if m < 3 else 1e-4
 
+    def fd(j, m, h):
         def L(tj):
             Ph = oracle.compose(Pn[j:j + 1], tj[None])
             v = oracle.bp_forward(Ph, pj[j:j + 1], cfg.vol_shape, cfg.spacing3, cfg.origin,
                                   vw[j:j + 1], oracle.WEIGHT_FDK, cfg.sid)
             return float(np.sum(dl * v))
-
         tp, tm = thn[j].copy(), thn[j].copy()
         tp[m] += h
         tm[m] -= h
-        fd = (L(tp) - L(tm)) / (2 * h)
+        return (L(tp) - L(tm)) / (2 * h)
+
+    fine, coarse = [], []
+    for j, m in picks:
         scale = np.abs(g[:, m]).max()
-        rel.append(abs(fd - g[j, m]) / max(abs(fd), 1e-2 * scale))
-    rel = np.array(rel)
-    # bilinear kinks: an FD interval that straddles a pixel boundary averages
-    # two slopes, so a few parameters may differ more
-    assert np.median(rel) < 1e-3, rel
-    assert np.mean(rel < 1e-2) >= 0.9, rel
+        for out, h in ((fine, 1e-7 if m < 3 else 1e-9), (coarse, 1e-3 if m < 3 else 1e-4)):
+            f = fd(j, m, h)
+            out.append(abs(f - g[j, m]) / max(abs(f), 1e-2 * scale))
+    fine, coarse = np.array(fine), np.array(coarse)
+    assert np.median(fine) < 1e-3, fine
+    assert np.mean(fine < 1e-2) >= 0.9, fine
+    assert np.median(coarse) < 1e-1, coarse
 
 
 def test_fd_projection_gradient_c4g():

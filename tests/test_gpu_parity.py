@@ -297,6 +297,16 @@ def test_sharpness_matches_oracle():
     assert np.abs(g.cpu().numpy() - go).max() <= 1e-5 * np.abs(go).max()
 
 
+def test_tv_matches_oracle():
+    rng = np.random.default_rng(4)
+    vol = rng.standard_normal((13, 17, 19)).astype(np.float32)
+    for eps in (1e-3, 0.5):
+        L, g = bp.bp_tv(cuda(vol), eps)
+        Lo, go = oracle.tv(vol.astype(np.float64), eps)
+        assert abs(float(L) - Lo) <= 1e-6 * abs(Lo)
+        assert np.abs(g.cpu().numpy() - go).max() <= 1e-5 * np.abs(go).max()
+
+
 def test_optimisers_match_oracle():
     rng = np.random.default_rng(1)
     th = rng.standard_normal((50, 6))

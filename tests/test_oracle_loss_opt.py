@@ -65,3 +65,32 @@ def test_adam_first_steps_closed_form():
     mh = (0.9 * 0.1 * g1 + 0.1 * g2) / (1 - 0.9 ** 2)
     vh = (0.999 * 0.001 * g1 ** 2 + 0.001 * g2 ** 2) / (1 - 0.999 ** 2)
     assert np.allclose(t2, t1 - lr * mh / (np.sqrt(vh) + 1e-8), atol=1e-14)
+
+
+def test_tv_closed_forms():
+    nz, ny, nx = 5, 6, 7
+    K = nx * ny * nz
+    n_int = (nx - 1) * (ny - 1) * (nz - 1)
+    eps = 1e-2
+    L, g = oracle.tv(np.full((nz, ny, nx), 2.5), eps)
+    assert L == pytest.approx(n_int * eps / K, rel=1e-14)
+    assert np.all(g == 0.0)
+    a = 0.3
+    ramp = a * np.arange(nx)[None, None, :] * np.ones((nz, ny, nx))
+    L, g = oracle.tv(ramp, eps)
+    assert L == pytest.approx(n_int * np.sqrt(a * a + eps * eps) / K, rel=1e-14)
+    assert abs(g.sum()) < 1e-14
+
+
+def test_tv_gradient_fd():
+    rng = np.random.default_rng(3)
+    vol = rng.standard_normal((8, 8, 8))
+    eps = 0.05
+    L, g = oracle.tv(vol, eps)
+    h = 1e-6
+    for idx in [(0, 0, 0), (3, 4, 5), (7, 7, 7), (0, 7, 3), (4, 0, 7), (7, 3, 0)]:
+        vp, vm = vol.copy(), vol.copy()
+        vp[idx] += h
+        vm[idx] -= h
+        fd = (oracle.tv(vp, eps, False)[0] - oracle.tv(vm, eps, False)[0]) / (2 * h)
+        assert abs(fd - g[idx]) < 1e-8
