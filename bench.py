@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--quick", action="store_true", help="skip clocks/e2e/cpu legs (profiling)")
+    ap.add_argument("--me-iters", type=int, default=100, help="motion-estimation leg iterations")
+    ap.add_argument("--serving", type=int, default=0, help="jobs of the serving leg (0 = skip)")
     return ap.parse_args()
 
 
@@ -256,6 +258,17 @@ def run_ours(args):
 
     if not args.no_e2e and not args.quick:
         out["e2e"] = e2e_leg(args, cfg, P, proj, vw, geo, dev)
+    if not args.quick and args.me_iters > 0:
+        out["motion_estimation"] = motion_estimation_leg(args, cfg, P, th_true, proj, vw, dev)
+    if args.serving > 0 and rank == 0:
+        from paper_2401_09283_gb300 import serving as S
+        reqs = S.make_requests(args.serving, 4.0, 5, "fp16", device=local)
+        srv = S.Server(device=local, slots=4)
+        res = srv.run(reqs)
+        out["serving"] = {"served_fp16": S.summarize(res, reqs, srv)}
+        reqs32 = S.make_requests(args.serving, 4.0, 5, "fp32", device=local)
+        out["serving"]["sequential_fp32"] = S.summarize(S.run_sequential(reqs32, device=local),
+                                                        reqs32, None)
     if ws > 1:
         torch.distributed.barrier()
     if rank == 0 and not args.no_cpu and not args.quick and ws == 1:
@@ -264,6 +277,43 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def motion_estimation_leg(args, cfg, P, th_true, proj, vw, dev):
+    """Config-2 motion estimation through the job API (device-resident state,
+    one CUDA graph per iteration): time per iteration and RPE before/after,
+    with the configured sharpness loss and with total variation."""
+    import torch
+
+    import paper_2401_09283_gb300.workloads as W
+    from paper_2401_09283_gb300 import bp
+    from paper_2401_09283_gb300.job import MotionJob
+    from paper_2401_09283_gb300.metrics import reprojection_error
+    Pd = torch.as_tensor(P, device=dev)
+    pts = W.rpe_points()
+    true = bp.bp_compose(Pd, torch.as_tensor(th_true, device=dev)).cpu().numpy()
+    out = {"iters": args.me_iters, "optimizer": "adam", "lr_mm": 0.05, "lr_rad": 5e-4,
+           "rpe_before_mm": reprojection_error(P, true, pts, cfg.pitch, cfg.pitch)}
+    geo = dict(vol_shape=cfg.vol_shape, spacing=cfg.spacing3, origin=cfg.origin, sid=cfg.sid)
+    for loss in ("sharpness", "tv"):
+        job = MotionJob(proj, Pd, view_weight=vw, optimizer="adam", lr=0.05, lr_rot=5e-4,
+                        max_iters=args.me_iters, loss=loss, **geo)
+        s = torch.cuda.current_stream(dev)
+        job.step(2, s.cuda_stream)  # capture + warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        job.step(args.me_iters - 2, s.cuda_stream)
+        e1.record(s)
+        th, hist, it = job.motion()
+        ms = e0.elapsed_time(e1) / (args.me_iters - 2)
+        job.close()
+        est = bp.bp_compose(Pd, torch.as_tensor(th, device=dev)).cpu().numpy()
+        out[loss] = {"ms_per_iter": ms, "iters_done": it,
+                     "rpe_after_mm": reprojection_error(est, true, pts, cfg.pitch, cfg.pitch),
+                     "loss_first": float(hist[0]), "loss_last": float(hist[it - 1])}
+    out["jobs_per_s"] = 1000.0 / (out["sharpness"]["ms_per_iter"] * args.me_iters)
+    return out
 
 
 def e2e_leg(args, cfg, P, proj, vw, geo, dev):

@@ -80,7 +80,7 @@ size_t proj_bytes(const bp_proj_desc* pd) {
   return (size_t)elems * dtype_size(pd->dtype);
 }
 
-constexpr int ZB = 16;
+constexpr int ZB = bpk::ZB_VJP;
 
 // Stage the per-view inputs and run the FP64 composition into ctx->geom.
 int prepare_views(bp_ctx* ctx, const bp_proj_desc* pd, const double* P, const double* motion,

@@ -28,6 +28,12 @@ constexpr int NT = TX * TY;   // threads per CTA
 constexpr int VB = 32;        // views per FP64 set-up batch
 constexpr int PSLOTS = 16;    // floats per (tile, view) partial record
 
+// z-extent of the VJP tiles (the tiling of the per-tile partial records)
+#ifndef BP_ZB_VJP
+#define BP_ZB_VJP 16
+#endif
+constexpr int ZB_VJP = BP_ZB_VJP;
+
 // Per view, written by compose_kernel.
 struct ViewGeom {
   double P[12];   // P' = P T(theta) A   (index frame -> absolute pixels)

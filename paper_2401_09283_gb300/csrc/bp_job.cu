@@ -35,7 +35,7 @@ struct bp_job {
 
 namespace {
 
-constexpr int ZB = 16;
+constexpr int ZB = bpk::ZB_VJP;
 constexpr long long kAlign = 256;
 
 long long align_up(long long x) { return (x + kAlign - 1) / kAlign * kAlign; }

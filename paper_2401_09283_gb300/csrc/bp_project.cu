@@ -446,8 +446,14 @@ __global__ void __launch_bounds__(NT, FWD_MINB)
   }
 }
 
-constexpr int ZB_FWD = 16;
-constexpr int ZB_VJP = 16;
+// z-extent of the forward's tiles (its own tiling; the VJP's is ZB_VJP)
+#ifndef BP_ZB_FWD
+#define BP_ZB_FWD 16
+#endif
+#ifndef BP_FWD_STAGE
+#define BP_FWD_STAGE 1
+#endif
+constexpr int ZB_FWD = BP_ZB_FWD;
 
 // Staging needs 16-byte aligned rows and whole 16-byte chunks per row.
 template <typename T>
@@ -476,7 +482,7 @@ static cudaError_t forward_dispatch(const void* proj, const ProjInfo& pi, const 
                                     const VolInfo& vi, float* vol, cudaStream_t s) {
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
   const int smem = 2 * STAGE_BYTES;
-  if (stageable<T>(proj, pi)) {
+  if (BP_FWD_STAGE && stageable<T>(proj, pi)) {
     cudaError_t e = smem_attr_once<forward_kernel<ZB_FWD, T, FDK, true>>(smem);
     if (e != cudaSuccess) return e;
     forward_kernel<ZB_FWD, T, FDK, true><<<ntiles, NT, smem, s>>>((const T*)proj, pi, geom, vi, vol);
@@ -499,8 +505,10 @@ cudaError_t prepare_forward(int dtype, int fdk) {
 }
 
 cudaError_t launch_forward(const void* proj, int dtype, const ProjInfo& pi, const ViewGeom* geom,
-                           const VolInfo& vi, int fdk, float* vol, cudaStream_t s) {
-  if (vi.zb != ZB_FWD) return cudaErrorInvalidValue;
+                           const VolInfo& vi_in, int fdk, float* vol, cudaStream_t s) {
+  VolInfo vi = vi_in;  // the forward tiles z by ZB_FWD
+  vi.zb = ZB_FWD;
+  vi.tiles_z = (vi.nz + ZB_FWD - 1) / ZB_FWD;
   if (dtype == 0)
     return fdk ? forward_dispatch<float, true>(proj, pi, geom, vi, vol, s)
                : forward_dispatch<float, false>(proj, pi, geom, vi, vol, s);
