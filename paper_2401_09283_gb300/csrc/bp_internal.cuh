@@ -55,6 +55,13 @@ struct TileView {
   int fw, fh;         // footprint size in pixels (0 when unbounded)
   int csafe;          // every tap pixel and its central-difference neighbours
                       // (one more pixel each side) lie inside the detector
+  // Staged footprint in shared memory (staged != 0): detector rows
+  // [sv0, sv0 + sh) and 16-byte chunks [sx0, sx0 + scpr * CH) at a fixed row
+  // pitch, zero where they lie off the detector.  soff turns the
+  // magic-number floor bits (bx, by) of a sample into its element index
+  // by * pitch + bx + soff (mod 2^32); srpp rows are copied per warp pass and
+  // smag = ceil(2^16 / scpr) divides a lane index by scpr.
+  int sx0, sv0, sh, scpr, srpp, smag, soff, staged;
 };
 
 enum { MODE_SKIP = 0, MODE_INTERIOR = 1, MODE_EDGE = 2 };

@@ -29,6 +29,17 @@ constexpr int VJP_MINB = BP_VJP_MINB;
 constexpr float MAGIC = 12582912.0f;   // 1.5 * 2^23
 constexpr int MAGIC_BITS = 0x4B400000;
 
+// Footprint staging buffers: fixed row pitch (so tap offsets are
+// immediates), rows of 22 16-byte chunks, 64 rows.
+constexpr int STAGE_PITCH_BYTES = 352;
+constexpr int STAGE_ROWS = 64;
+constexpr int STAGE_BYTES = STAGE_PITCH_BYTES * STAGE_ROWS;
+template <typename T>
+struct StageGeom {
+  static constexpr int CH = 16 / (int)sizeof(T);                // elements per chunk
+  static constexpr int P = STAGE_PITCH_BYTES / (int)sizeof(T);  // row pitch in elements
+};
+
 template <typename T>
 __device__ __forceinline__ float ldv(const T* p);
 template <>
@@ -94,8 +105,16 @@ __device__ __forceinline__ TileIdx tile_index(const VolInfo& vi, int tile) {
 //   EDGE      otherwise (clamped coordinates, checked taps).
 // The footprint is the clipped pixel rectangle that the box's taps can
 // touch (unbounded, fw = 0, when some corner has w <= 0).
+//
+// With STAGE, bounded boxes also get a staging plan: the rectangle of
+// detector pixels that any tap (plus `halo` pixels each side) can read,
+// NOT clipped to the detector (off-detector pixels are staged as zeros, so
+// the sample loop needs neither checks nor clamps), if it fits the buffer.
+// With `need_csafe` only central-safe boxes are staged.
+template <typename T, bool STAGE>
 __device__ void setup_batch(TileView* tvs, const ViewGeom* __restrict__ geom, int j0, int nb,
-                            const TileIdx& ti, int nu, int nv, bool with_scale) {
+                            const TileIdx& ti, int nu, int nv, bool with_scale, int halo = 0,
+                            bool need_csafe = false) {
   const int b = threadIdx.x >> 3, c = threadIdx.x & 7;
   const ViewGeom& g = geom[j0 + min(b, nb - 1)];
   const double* M = g.P;
@@ -154,6 +173,7 @@ __device__ void setup_batch(TileView* tvs, const ViewGeom* __restrict__ geom, in
   const float ulo = -fau, uhi = (float)(nu - 1) - fau, vlo = -fav, vhi = (float)(nv - 1) - fav;
   t.fu0 = t.fv0 = t.fw = t.fh = 0;
   t.csafe = 0;
+  t.sx0 = t.sv0 = t.sh = t.scpr = t.srpp = t.smag = t.soff = t.staged = 0;
   if (npos == 0) {
     t.mode = MODE_SKIP;
   } else if (npos < 8) {
@@ -169,13 +189,33 @@ __device__ void setup_batch(TileView* tvs, const ViewGeom* __restrict__ geom, in
     // taps in [1, n-2], i.e. floor in [1, n-3]
     t.csafe = xmin >= ulo + 1.0f + m && xmax <= uhi - 1.0f - m && ymin >= vlo + 1.0f + m &&
               ymax <= vhi - 1.0f - m;
-    const int u0 = max((int)floorf(xmin - m) + au, 0), u1 = min((int)floorf(xmax + m) + 1 + au, nu - 1);
-    const int v0 = max((int)floorf(ymin - m) + av, 0), v1 = min((int)floorf(ymax + m) + 1 + av, nv - 1);
+    const int fl_u0 = (int)floorf(xmin - m) + au, fl_u1 = (int)floorf(xmax + m) + 1 + au;
+    const int fl_v0 = (int)floorf(ymin - m) + av, fl_v1 = (int)floorf(ymax + m) + 1 + av;
+    const int u0 = max(fl_u0, 0), u1 = min(fl_u1, nu - 1);
+    const int v0 = max(fl_v0, 0), v1 = min(fl_v1, nv - 1);
     if (u1 >= u0 && v1 >= v0) {
       t.fu0 = u0;
       t.fv0 = v0;
       t.fw = u1 - u0 + 1;
       t.fh = v1 - v0 + 1;
+    }
+    if (STAGE && t.mode != MODE_SKIP && (!need_csafe || t.csafe)) {
+      constexpr int CH = StageGeom<T>::CH, P = StageGeom<T>::P;
+      const int x0 = (fl_u0 - halo) & ~(CH - 1);  // floor to a chunk boundary
+      const int y0 = fl_v0 - halo;
+      const int cpr = (fl_u1 + halo - x0) / CH + 1;
+      const int h = fl_v1 + halo - y0 + 1;
+      if (cpr * CH <= P && h <= STAGE_ROWS) {
+        t.staged = 1;
+        t.sx0 = x0;
+        t.sv0 = y0;
+        t.sh = h;
+        t.scpr = cpr;
+        t.srpp = 32 / cpr;
+        t.smag = (65536 + cpr - 1) / cpr;
+        t.soff = (int)((unsigned)(av - y0) * (unsigned)P - (unsigned)MAGIC_BITS * (unsigned)P +
+                       (unsigned)(au - x0) - (unsigned)MAGIC_BITS);
+      }
     }
   }
   tvs[b] = t;
@@ -187,6 +227,7 @@ struct Sample {
   float x, y;    // u/w - au, v/w - av (clamped in EDGE mode)
   float tu, tv;  // fractional parts
   int iu, iv;    // absolute floor pixel
+  int bx, by;    // bit patterns of x + MAGIC, y + MAGIC (rounded down)
   bool ok;       // w > 0
 };
 
@@ -209,8 +250,10 @@ __device__ __forceinline__ Sample locate(float u, float v, float w, const TileVi
   float rx = __fadd_rd(x, MAGIC), ry = __fadd_rd(y, MAGIC);
   s.tu = x - (rx - MAGIC);
   s.tv = y - (ry - MAGIC);
-  s.iu = __float_as_int(rx) - MAGIC_BITS + t.au;
-  s.iv = __float_as_int(ry) - MAGIC_BITS + t.av;
+  s.bx = __float_as_int(rx);
+  s.by = __float_as_int(ry);
+  s.iu = s.bx - MAGIC_BITS + t.au;
+  s.iv = s.by - MAGIC_BITS + t.av;
   s.x = x;
   s.y = y;
   return s;
@@ -249,12 +292,11 @@ __device__ __forceinline__ float bilerp(float tu, float tv, float d00, float d10
 // Each (tile, view) reads a small rectangle of one detector image (the tile
 // footprint from the set-up).  Voxels project ~2.6 px apart on the larger
 // detectors, so a warp's 32 taps of one load are scattered over 4-6 L1
-// lines; from shared memory the same taps are a single conflict-free
-// wavefront.  The footprint (plus an optional halo) is therefore copied to
-// shared memory with cp.async in 16-byte chunks, double-buffered across
-// views: the copy of view j+1 overlaps the arithmetic of view j.  Footprints
-// that do not fit the buffer, or are unbounded, read global memory instead.
-constexpr int STAGE_BYTES = 24576;  // per buffer; two buffers per CTA
+// lines; from shared memory the same taps are a single wavefront (bar bank
+// conflicts).  The footprint is therefore copied to shared memory with
+// cp.async in 16-byte chunks, one view ahead: the copy of view j+1 overlaps
+// the arithmetic of view j.  Footprints that do not fit the buffer, or are
+// unbounded, read global memory instead.
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -267,42 +309,27 @@ __device__ __forceinline__ void cp_async_wait1() {
   asm volatile("cp.async.wait_group 1;\n" ::: "memory");
 }
 
-// A staged rectangle: rows [v0, v0+h), columns [x0, x0 + cpr*CH), stored
-// with row pitch `pitch` elements.
-struct Stage {
-  int x0, v0, h, pitch, cpr;
-  bool on;
-};
-
+// All threads: copy the staged rectangle of record t (rows per warp pass,
+// one chunk per lane, no divisions).  A chunk lies wholly on or off the
+// detector (chunk starts are multiples of CH and nu is), so off-detector
+// chunks and rows are written as zeros.
 template <typename T>
-__device__ __forceinline__ Stage stage_plan(const TileView& t, int halo, int nu, int nv) {
-  constexpr int CH = 16 / (int)sizeof(T);
-  Stage st;
-  st.on = false;
-  st.x0 = st.v0 = st.h = st.pitch = st.cpr = 0;
-  if (t.mode == MODE_SKIP || t.fw <= 0) return st;
-  const int u0 = max(t.fu0 - halo, 0), u1 = min(t.fu0 + t.fw - 1 + halo, nu - 1);
-  const int v0 = max(t.fv0 - halo, 0), v1 = min(t.fv0 + t.fh - 1 + halo, nv - 1);
-  st.x0 = u0 & ~(CH - 1);
-  st.cpr = (u1 - st.x0) / CH + 1;
-  st.pitch = (st.cpr + 1) * CH;  // one spare chunk per row staggers the banks
-  st.v0 = v0;
-  st.h = v1 - v0 + 1;
-  st.on = st.cpr <= 32 && st.pitch * st.h * (int)sizeof(T) <= STAGE_BYTES;
-  return st;
-}
-
-// All threads: issue the copies of one staged rectangle (rows per warp,
-// chunks per lane, no divisions per chunk).
-template <typename T>
-__device__ __forceinline__ void stage_issue(T* buf, const T* img, long long rs, const Stage& st) {
-  constexpr int CH = 16 / (int)sizeof(T);
+__device__ __forceinline__ void stage_issue(T* buf, const T* img, long long rs, int nu, int nv,
+                                            const TileView& t) {
+  constexpr int CH = StageGeom<T>::CH, P = StageGeom<T>::P;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rpp = 32 / st.cpr;  // rows per warp pass
-  const int lr = lane / st.cpr, lc = lane - lr * st.cpr;
-  if (lr >= rpp) return;
-  for (int r = warp * rpp + lr; r < st.h; r += (NT / 32) * rpp)
-    cp_async16(buf + r * st.pitch + lc * CH, img + (long long)(st.v0 + r) * rs + st.x0 + lc * CH);
+  const int lr = (lane * t.smag) >> 16, lc = lane - lr * t.scpr;
+  if (lr >= t.srpp) return;
+  const int cu = t.sx0 + lc * CH;
+  const bool uin = cu >= 0 && cu < nu;
+  for (int r = warp * t.srpp + lr; r < t.sh; r += (NT / 32) * t.srpp) {
+    T* dst = buf + r * P + lc * CH;
+    const int row = t.sv0 + r;
+    if (uin && (unsigned)row < (unsigned)nv)
+      cp_async16(dst, img + (long long)row * rs + cu);
+    else
+      *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+  }
 }
 
 template <typename T>
@@ -320,39 +347,21 @@ __device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 x) {
   return __bfloat162float(x);
 }
 
-// Four taps from a staged rectangle, zero outside the detector.
-template <bool EDGE, typename T>
-__device__ __forceinline__ void taps_smem(const T* buf, const Stage& st, int nu, int nv,
-                                          const Sample& s, float& d00, float& d10, float& d01,
-                                          float& d11) {
-  const int o = (s.iv - st.v0) * st.pitch + (s.iu - st.x0);
-  if (!EDGE) {
-    d00 = tof(buf[o]);
-    d10 = tof(buf[o + 1]);
-    d01 = tof(buf[o + st.pitch]);
-    d11 = tof(buf[o + st.pitch + 1]);
-  } else {
-    // off-detector taps may lie outside the staged rectangle: read a safe
-    // address and discard
-    const bool u0 = (unsigned)s.iu < (unsigned)nu, u1 = (unsigned)(s.iu + 1) < (unsigned)nu;
-    const bool v0 = (unsigned)s.iv < (unsigned)nv, v1 = (unsigned)(s.iv + 1) < (unsigned)nv;
-    const bool k00 = u0 && v0 && s.ok, k10 = u1 && v0 && s.ok;
-    const bool k01 = u0 && v1 && s.ok, k11 = u1 && v1 && s.ok;
-    const float a = tof(buf[k00 ? o : 0]), b = tof(buf[k10 ? o + 1 : 0]);
-    const float c = tof(buf[k01 ? o + st.pitch : 0]), d = tof(buf[k11 ? o + st.pitch + 1 : 0]);
-    d00 = k00 ? a : 0.0f;
-    d10 = k10 ? b : 0.0f;
-    d01 = k01 ? c : 0.0f;
-    d11 = k11 ? d : 0.0f;
-  }
+// A sample's position in the staged buffer: (bx, by) are the bit patterns
+// of x + MAGIC and y + MAGIC rounded down, i.e. MAGIC_BITS + floor.
+template <typename T>
+__device__ __forceinline__ const T* staged_tap(const T* buf, const TileView& t, int bx, int by) {
+  const unsigned o = (unsigned)by * (unsigned)StageGeom<T>::P + (unsigned)bx + (unsigned)t.soff;
+  return buf + (int)o;
 }
 
 // ------------------------------------------------------------------ forward
 
-template <int ZB, typename T, bool FDK, bool EDGE, bool SMEM>
-__device__ __forceinline__ void forward_view(const T* img, const T* buf, const Stage& st,
-                                             long long rs, int nu, int nv, const TileView& t,
-                                             float dx, float dy, float (&acc)[ZB]) {
+// One view from global memory (footprint not staged).
+template <int ZB, typename T, bool FDK, bool EDGE>
+__device__ __forceinline__ void forward_view(const T* img, long long rs, int nu, int nv,
+                                             const TileView& t, float dx, float dy,
+                                             float (&acc)[ZB]) {
   float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
   float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
   float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
@@ -363,19 +372,42 @@ __device__ __forceinline__ void forward_view(const T* img, const T* buf, const S
                             t, nu, nv);
     if (EDGE && !s.ok) continue;
     float d00, d10, d01, d11;
-    if (SMEM)
-      taps_smem<EDGE>(buf, st, nu, nv, s, d00, d10, d01, d11);
-    else
-      taps<EDGE>(img, rs, nu, nv, s, d00, d10, d01, d11);
+    taps<EDGE>(img, rs, nu, nv, s, d00, d10, d01, d11);
     float val = bilerp(s.tu, s.tv, d00, d10, d01, d11);
     float wv = FDK ? s.rwi * (s.rwi * t.wgt) : t.wgt;
     acc[k] = fmaf(val, wv, acc[k]);
   }
 }
 
+// One view from its staged, zero-padded footprint: no checks, no clamps,
+// tap offsets are compile-time constants.
+template <int ZB, typename T, bool FDK>
+__device__ __forceinline__ void forward_view_staged(const T* buf, const TileView& t, float dx,
+                                                    float dy, float (&acc)[ZB]) {
+  constexpr int P = StageGeom<T>::P;
+  const float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
+  const float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
+  const float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
+#pragma unroll
+  for (int k = 0; k < ZB; ++k) {
+    const float dz = k - 0.5f * (ZB - 1);
+    const Sample s = locate<false>(fmaf(dz, t.ru[2], u0), fmaf(dz, t.rv[2], v0),
+                                   fmaf(dz, t.rw[2], w0), t, 0, 0);
+    const T* q = staged_tap(buf, t, s.bx, s.by);
+    const float val = bilerp(s.tu, s.tv, tof(q[0]), tof(q[1]), tof(q[P]), tof(q[P + 1]));
+    const float wv = FDK ? s.rwi * (s.rwi * t.wgt) : t.wgt;
+    acc[k] = fmaf(val, wv, acc[k]);
+  }
+}
+
 // Views are processed in order; the records of batch k+1 are built at the
 // start of batch k (two record slots), so the footprint of view j+1 is
-// known, and its copy issued, while view j is computed.
+// known, and its copy issued, while view j is computed.  Three staging
+// buffers: the copy into buffer (j+1) mod 3 cannot overlap a read of it
+// (view j-2, finished by every thread before the barrier of view j-1), so
+// one barrier per view suffices.
+constexpr int FWD_NBUF = 3;
+
 template <int ZB, typename T, bool FDK, bool STAGE>
 __global__ void __launch_bounds__(NT, FWD_MINB)
     forward_kernel(const T* __restrict__ proj, ProjInfo pi, const ViewGeom* __restrict__ geom,
@@ -390,51 +422,42 @@ __global__ void __launch_bounds__(NT, FWD_MINB)
   for (int k = 0; k < ZB; ++k) acc[k] = 0.0f;
   const int V = pi.nviews;
   const int nbatch = (V + VB - 1) / VB;
-  setup_batch(tvs[0], geom, 0, min(VB, V), ti, pi.nu, pi.nv, true);
-  if (nbatch > 1) setup_batch(tvs[1], geom, VB, min(VB, V - VB), ti, pi.nu, pi.nv, true);
+  setup_batch<T, STAGE>(tvs[0], geom, 0, min(VB, V), ti, pi.nu, pi.nv, true);
+  if (nbatch > 1) setup_batch<T, STAGE>(tvs[1], geom, VB, min(VB, V - VB), ti, pi.nu, pi.nv, true);
   __syncthreads();
-  Stage st_cur = STAGE ? stage_plan<T>(tvs[0][0], 0, pi.nu, pi.nv) : Stage{0, 0, 0, 0, 0, false};
-  if (STAGE && st_cur.on) stage_issue(bufs, proj, pi.rs, st_cur);
+  if (STAGE && V > 0 && tvs[0][0].staged) stage_issue(bufs, proj, pi.rs, pi.nu, pi.nv, tvs[0][0]);
   cp_async_commit();
+  int cur = 0;  // buffer of view v
   for (int v = 0; v < V; ++v) {
     const int k = v / VB, b = v - k * VB;
     if (b == 0 && k >= 1 && k + 1 < nbatch) {
-      setup_batch(tvs[(k + 1) & 1], geom, (k + 1) * VB, min(VB, V - (k + 1) * VB), ti, pi.nu,
-                  pi.nv, true);
+      setup_batch<T, STAGE>(tvs[(k + 1) & 1], geom, (k + 1) * VB, min(VB, V - (k + 1) * VB), ti,
+                            pi.nu, pi.nv, true);
       __syncthreads();
     }
     const TileView t = tvs[k & 1][b];
-    Stage st_next = Stage{0, 0, 0, 0, 0, false};
+    const int nxt = cur == FWD_NBUF - 1 ? 0 : cur + 1;
     if (STAGE && v + 1 < V) {
       const int kn = (v + 1) / VB;
-      st_next = stage_plan<T>(tvs[kn & 1][v + 1 - kn * VB], 0, pi.nu, pi.nv);
-      if (st_next.on)
-        stage_issue(bufs + ((v + 1) & 1) * CAP, proj + (long long)(v + 1) * pi.vs, pi.rs, st_next);
+      const TileView& tn = tvs[kn & 1][v + 1 - kn * VB];
+      if (tn.staged)
+        stage_issue(bufs + nxt * CAP, proj + (long long)(v + 1) * pi.vs, pi.rs, pi.nu, pi.nv, tn);
     }
     cp_async_commit();
     cp_async_wait1();
     __syncthreads();
     if (t.mode != MODE_SKIP) {
-      const T* img = proj + (long long)v * pi.vs;
-      const T* buf = bufs + (v & 1) * CAP;
-      if (st_cur.on) {
-        if (t.mode == MODE_INTERIOR)
-          forward_view<ZB, T, FDK, false, true>(img, buf, st_cur, pi.rs, pi.nu, pi.nv, t, ti.dx,
-                                                ti.dy, acc);
-        else
-          forward_view<ZB, T, FDK, true, true>(img, buf, st_cur, pi.rs, pi.nu, pi.nv, t, ti.dx,
-                                               ti.dy, acc);
+      if (STAGE && t.staged) {
+        forward_view_staged<ZB, T, FDK>(bufs + cur * CAP, t, ti.dx, ti.dy, acc);
       } else {
+        const T* img = proj + (long long)v * pi.vs;
         if (t.mode == MODE_INTERIOR)
-          forward_view<ZB, T, FDK, false, false>(img, buf, st_cur, pi.rs, pi.nu, pi.nv, t, ti.dx,
-                                                 ti.dy, acc);
+          forward_view<ZB, T, FDK, false>(img, pi.rs, pi.nu, pi.nv, t, ti.dx, ti.dy, acc);
         else
-          forward_view<ZB, T, FDK, true, false>(img, buf, st_cur, pi.rs, pi.nu, pi.nv, t, ti.dx,
-                                                ti.dy, acc);
+          forward_view<ZB, T, FDK, true>(img, pi.rs, pi.nu, pi.nv, t, ti.dx, ti.dy, acc);
       }
     }
-    __syncthreads();
-    st_cur = st_next;
+    cur = nxt;
   }
   const int i = ti.tx * TX + ti.lx, j = ti.ty * TY + ti.ly;
   if (i < vi.nx && j < vi.ny) {
@@ -481,7 +504,7 @@ template <typename T, bool FDK>
 static cudaError_t forward_dispatch(const void* proj, const ProjInfo& pi, const ViewGeom* geom,
                                     const VolInfo& vi, float* vol, cudaStream_t s) {
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
-  const int smem = 2 * STAGE_BYTES;
+  const int smem = FWD_NBUF * STAGE_BYTES;
   if (BP_FWD_STAGE && stageable<T>(proj, pi)) {
     cudaError_t e = smem_attr_once<forward_kernel<ZB_FWD, T, FDK, true>>(smem);
     if (e != cudaSuccess) return e;
@@ -493,7 +516,7 @@ static cudaError_t forward_dispatch(const void* proj, const ProjInfo& pi, const 
 }
 
 cudaError_t prepare_forward(int dtype, int fdk) {
-  const int smem = 2 * STAGE_BYTES;
+  const int smem = FWD_NBUF * STAGE_BYTES;
   if (dtype == 0)
     return fdk ? smem_attr_once<forward_kernel<ZB_FWD, float, true, true>>(smem)
                : smem_attr_once<forward_kernel<ZB_FWD, float, false, true>>(smem);
@@ -646,27 +669,38 @@ __device__ __forceinline__ int scatter_slot(int lane) {
 //               the one-sided edge rule).
 enum { SRC_GLOBAL = 0, SRC_SMEM = 1 };
 
+//
+// A staged footprint is zero-padded and covers every tap, so with SRC_SMEM
+// the coordinates are never clamped (EDGE then only guards the scatter of
+// the fused data VJP).
 template <int ZB, typename T, bool FDK, bool EXACT, bool EDGE, bool PROJ, int SRC>
 __device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, const T* buf,
-                                         const Stage& st, float* pout, long long rs, int nu,
-                                         int nv, const TileView& t, float dx, float dy,
+                                         float* pout, long long rs, int nu, int nv,
+                                         const TileView& t, float dx, float dy,
                                          const float (&delta)[ZB], float (&S)[3], float (&Z)[3]) {
+  constexpr bool CLAMP = EDGE && SRC == SRC_GLOBAL;
+  constexpr int P = StageGeom<T>::P;
   float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
   float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
   float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
 #pragma unroll
   for (int k = 0; k < ZB; ++k) {
     const float dz = k - 0.5f * (ZB - 1);
-    Sample s = locate<EDGE>(fmaf(dz, t.ru[2], u0), fmaf(dz, t.rv[2], v0), fmaf(dz, t.rw[2], w0),
-                            t, nu, nv);
-    if (EDGE && !s.ok) continue;
+    Sample s = locate<CLAMP>(fmaf(dz, t.ru[2], u0), fmaf(dz, t.rv[2], v0), fmaf(dz, t.rw[2], w0),
+                             t, nu, nv);
+    if (CLAMP && !s.ok) continue;
     float gu, gv, val = 0.0f, gscale = 1.0f;
     if (EXACT) {
       float d00, d10, d01, d11;
-      if (SRC == SRC_SMEM)
-        taps_smem<EDGE>(buf, st, nu, nv, s, d00, d10, d01, d11);
-      else
+      if (SRC == SRC_SMEM) {
+        const T* q = staged_tap(buf, t, s.bx, s.by);
+        d00 = tof(q[0]);
+        d10 = tof(q[1]);
+        d01 = tof(q[P]);
+        d11 = tof(q[P + 1]);
+      } else {
         taps<EDGE>(img, rs, nu, nv, s, d00, d10, d01, d11);
+      }
       const float a = d10 - d00, b = d11 - d01;
       gu = fmaf(s.tv, b - a, a);
       const float c = d01 - d00, d = d11 - d10;
@@ -674,8 +708,8 @@ __device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, const
       if (FDK) val = bilerp(s.tu, s.tv, d00, d10, d01, d11);
     } else if (SRC == SRC_SMEM) {
       // central-safe interior tile: 12 staged taps around (iu, iv)
-      const int p = st.pitch;
-      const T* q = buf + (s.iv - st.v0) * p + (s.iu - st.x0);
+      constexpr int p = P;
+      const T* q = staged_tap(buf, t, s.bx, s.by);
       const float a0 = tof(q[-p]), a1 = tof(q[-p + 1]);
       const float b0 = tof(q[-1]), b1 = tof(q[0]), b2 = tof(q[1]), b3 = tof(q[2]);
       const float c0 = tof(q[p - 1]), c1 = tof(q[p]), c2 = tof(q[p + 1]), c3 = tof(q[p + 2]);
@@ -732,25 +766,24 @@ __device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, const
 // was staged), then the warp reduce-scatter of the 12 sums into red[][b].
 template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ>
 __device__ __forceinline__ void vjp_tile_view(const T* img, const float2* gimg, const T* buf,
-                                              const Stage& st, float* pout, const ProjInfo& pi,
+                                              bool staged, float* pout, const ProjInfo& pi,
                                               const TileView& t, const TileIdx& ti,
                                               const float (&delta)[ZB],
                                               float (*red)[VB][12], int b) {
   float S[3] = {0.0f, 0.0f, 0.0f}, Z[3] = {0.0f, 0.0f, 0.0f};
-  const bool smem = st.on && (EXACT || t.csafe);
-  if (smem) {
-    if (t.mode == MODE_INTERIOR)
-      vjp_view<ZB, T, FDK, EXACT, false, PROJ, SRC_SMEM>(img, gimg, buf, st, pout, pi.rs, pi.nu,
+  if (staged) {
+    if (t.mode == MODE_INTERIOR || !PROJ)
+      vjp_view<ZB, T, FDK, EXACT, false, PROJ, SRC_SMEM>(img, gimg, buf, pout, pi.rs, pi.nu,
                                                          pi.nv, t, ti.dx, ti.dy, delta, S, Z);
     else
-      vjp_view<ZB, T, FDK, EXACT, true, PROJ, SRC_SMEM>(img, gimg, buf, st, pout, pi.rs, pi.nu,
+      vjp_view<ZB, T, FDK, EXACT, true, PROJ, SRC_SMEM>(img, gimg, buf, pout, pi.rs, pi.nu,
                                                         pi.nv, t, ti.dx, ti.dy, delta, S, Z);
   } else {
     if (t.mode == MODE_INTERIOR)
-      vjp_view<ZB, T, FDK, EXACT, false, PROJ, SRC_GLOBAL>(img, gimg, buf, st, pout, pi.rs, pi.nu,
+      vjp_view<ZB, T, FDK, EXACT, false, PROJ, SRC_GLOBAL>(img, gimg, buf, pout, pi.rs, pi.nu,
                                                            pi.nv, t, ti.dx, ti.dy, delta, S, Z);
     else
-      vjp_view<ZB, T, FDK, EXACT, true, PROJ, SRC_GLOBAL>(img, gimg, buf, st, pout, pi.rs, pi.nu,
+      vjp_view<ZB, T, FDK, EXACT, true, PROJ, SRC_GLOBAL>(img, gimg, buf, pout, pi.rs, pi.nu,
                                                           pi.nv, t, ti.dx, ti.dy, delta, S, Z);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -822,16 +855,13 @@ __global__ void __launch_bounds__(NT, VJP_MINB)
   }
   const bool any = __syncthreads_or(nz);
   const int nvw = vend - vbeg, nbatch = (nvw + VB - 1) / VB;
-  setup_batch(tvs[0], geom, vbeg, min(VB, nvw), ti, pi.nu, pi.nv, true);
-  if (nbatch > 1) setup_batch(tvs[1], geom, vbeg + VB, min(VB, nvw - VB), ti, pi.nu, pi.nv, true);
+  setup_batch<T, STAGE>(tvs[0], geom, vbeg, min(VB, nvw), ti, pi.nu, pi.nv, true, HALO, !EXACT);
+  if (nbatch > 1)
+    setup_batch<T, STAGE>(tvs[1], geom, vbeg + VB, min(VB, nvw - VB), ti, pi.nu, pi.nv, true, HALO,
+                          !EXACT);
   __syncthreads();
-  auto plan = [&](const TileView& tv) {
-    Stage st = Stage{0, 0, 0, 0, 0, false};
-    if (STAGE && any && (EXACT || tv.csafe)) st = stage_plan<T>(tv, HALO, pi.nu, pi.nv);
-    return st;
-  };
-  Stage st_cur = plan(tvs[0][0]);
-  if (st_cur.on) stage_issue(bufs, proj + (long long)vbeg * pi.vs, pi.rs, st_cur);
+  if (STAGE && any && tvs[0][0].staged)
+    stage_issue(bufs, proj + (long long)vbeg * pi.vs, pi.rs, pi.nu, pi.nv, tvs[0][0]);
   cp_async_commit();
   for (int v = vbeg; v < vend; ++v) {
     const int idx = v - vbeg, k = idx / VB, b = idx - k * VB;
@@ -841,18 +871,17 @@ __global__ void __launch_bounds__(NT, VJP_MINB)
                       partials);
       __syncthreads();
       if (k + 1 < nbatch)
-        setup_batch(tvs[(k + 1) & 1], geom, vbeg + (k + 1) * VB, min(VB, nvw - (k + 1) * VB), ti,
-                    pi.nu, pi.nv, true);
+        setup_batch<T, STAGE>(tvs[(k + 1) & 1], geom, vbeg + (k + 1) * VB,
+                              min(VB, nvw - (k + 1) * VB), ti, pi.nu, pi.nv, true, HALO, !EXACT);
       __syncthreads();
     }
     const TileView t = tvs[k & 1][b];
-    Stage st_next = Stage{0, 0, 0, 0, 0, false};
-    if (STAGE && v + 1 < vend) {
+    if (STAGE && any && v + 1 < vend) {
       const int kn = (idx + 1) / VB;
-      st_next = plan(tvs[kn & 1][idx + 1 - kn * VB]);
-      if (st_next.on)
-        stage_issue(bufs + ((idx + 1) & 1) * CAP, proj + (long long)(v + 1) * pi.vs, pi.rs,
-                    st_next);
+      const TileView& tn = tvs[kn & 1][idx + 1 - kn * VB];
+      if (tn.staged)
+        stage_issue(bufs + ((idx + 1) & 1) * CAP, proj + (long long)(v + 1) * pi.vs, pi.rs, pi.nu,
+                    pi.nv, tn);
     }
     cp_async_commit();
     cp_async_wait1();
@@ -861,11 +890,10 @@ __global__ void __launch_bounds__(NT, VJP_MINB)
       const T* img = proj + (long long)v * pi.vs;
       const float2* gimg = EXACT ? nullptr : grad + (long long)v * pi.nv * pi.nu;
       float* pout = PROJ ? dproj + (long long)v * pi.nv * pi.nu : nullptr;
-      vjp_tile_view<ZB, T, FDK, EXACT, PROJ>(img, gimg, bufs + (idx & 1) * CAP, st_cur, pout, pi,
-                                             t, ti, delta, red, b);
+      vjp_tile_view<ZB, T, FDK, EXACT, PROJ>(img, gimg, bufs + (idx & 1) * CAP,
+                                             STAGE && t.staged, pout, pi, t, ti, delta, red, b);
     }
     __syncthreads();
-    st_cur = st_next;
   }
   if (nvw > 0) {
     const int kl = (nvw - 1) / VB;
@@ -1012,7 +1040,7 @@ __global__ void __launch_bounds__(NT, 2)
   for (int j0 = vbeg; j0 < vend; j0 += VB) {
     const int nb = min(VB, vend - j0);
     __syncthreads();
-    setup_batch(tvs, geom, j0, nb, ti, pi.nu, pi.nv, true);
+    setup_batch<float, false>(tvs, geom, j0, nb, ti, pi.nu, pi.nv, true);
     __syncthreads();
     for (int b = 0; b < nb; ++b) {
       const TileView t = tvs[b];
