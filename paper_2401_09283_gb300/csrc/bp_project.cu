@@ -18,7 +18,7 @@ namespace bpk {
 
 // CTAs per SM the register budget is sized for (256 threads each).
 #ifndef BP_FWD_MINB
-#define BP_FWD_MINB 3
+#define BP_FWD_MINB 4
 #endif
 #ifndef BP_VJP_MINB
 #define BP_VJP_MINB 3
@@ -30,8 +30,8 @@ constexpr float MAGIC = 12582912.0f;   // 1.5 * 2^23
 constexpr int MAGIC_BITS = 0x4B400000;
 
 // Footprint staging buffers: fixed row pitch (so tap offsets are
-// immediates), rows of 22 16-byte chunks, 64 rows.
-constexpr int STAGE_PITCH_BYTES = 352;
+// immediates), rows of 21 16-byte chunks, 64 rows.
+constexpr int STAGE_PITCH_BYTES = 336;
 constexpr int STAGE_ROWS = 64;
 constexpr int STAGE_BYTES = STAGE_PITCH_BYTES * STAGE_ROWS;
 template <typename T>
@@ -58,6 +58,46 @@ __device__ __forceinline__ float ldv<__nv_bfloat16>(const __nv_bfloat16* p) {
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Packed FP32 pairs (Blackwell f32x2 instructions): two voxels' values in
+// one 64-bit register, one instruction per pair.  Each element is rounded
+// exactly like the scalar instruction, so packed and scalar code give
+// identical results; the packing halves the issue slots of the FP32 work.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk2(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void up2(f2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 add2_rd(f2 a, f2 b) {  // rounded toward -inf
+  f2 r;
+  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
   return r;
 }
 
@@ -287,6 +327,12 @@ __device__ __forceinline__ float bilerp(float tu, float tv, float d00, float d10
   return fmaf(tv, bot - top, top);
 }
 
+__device__ __forceinline__ f2 bilerp2(f2 tu, f2 tv, f2 d00, f2 d10, f2 d01, f2 d11) {
+  const f2 top = fma2(tu, sub2(d10, d00), d00);
+  const f2 bot = fma2(tu, sub2(d11, d01), d01);
+  return fma2(tv, sub2(bot, top), top);
+}
+
 // ------------------------------------------------------ footprint staging
 
 // Each (tile, view) reads a small rectangle of one detector image (the tile
@@ -400,13 +446,53 @@ __device__ __forceinline__ void forward_view_staged(const T* buf, const TileView
   }
 }
 
+// The same from the staged footprint with packed pairs of voxels (k, k+1):
+// every step of the scalar loop above, in the same order, on f32x2 pairs.
+template <int ZB, typename T, bool FDK>
+__device__ __forceinline__ void forward_view_staged2(const T* buf, const TileView& t, float dx,
+                                                     float dy, f2 (&acc)[ZB / 2]) {
+  constexpr int P = StageGeom<T>::P;
+  const float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
+  const float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
+  const float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
+  const f2 U0 = pk2(u0, u0), V0 = pk2(v0, v0), W0 = pk2(w0, w0);
+  const f2 RU = pk2(t.ru[2], t.ru[2]), RV = pk2(t.rv[2], t.rv[2]), RW = pk2(t.rw[2], t.rw[2]);
+  const f2 M2 = pk2(MAGIC, MAGIC), TWO = pk2(2.0f, 2.0f), WG = pk2(t.wgt, t.wgt);
+  f2 dz = pk2(-0.5f * (ZB - 1), 1.0f - 0.5f * (ZB - 1));  // exact: halves of small integers
+#pragma unroll
+  for (int p = 0; p < ZB / 2; ++p) {
+    if (p) dz = add2(dz, TWO);
+    const f2 u = fma2(dz, RU, U0), v = fma2(dz, RV, V0), w = fma2(dz, RW, W0);
+    float wl, wh;
+    up2(w, wl, wh);
+    const f2 r = pk2(rcp_approx(wl), rcp_approx(wh));
+    const f2 x = mul2(u, r), y = mul2(v, r);
+    const f2 rx = add2_rd(x, M2), ry = add2_rd(y, M2);
+    const f2 tu = sub2(x, sub2(rx, M2)), tv = sub2(y, sub2(ry, M2));
+    float bxl, bxh, byl, byh;
+    up2(rx, bxl, bxh);
+    up2(ry, byl, byh);
+    const T* ql = staged_tap(buf, t, __float_as_int(bxl), __float_as_int(byl));
+    const T* qh = staged_tap(buf, t, __float_as_int(bxh), __float_as_int(byh));
+    const f2 d00 = pk2(tof(ql[0]), tof(qh[0])), d10 = pk2(tof(ql[1]), tof(qh[1]));
+    const f2 d01 = pk2(tof(ql[P]), tof(qh[P])), d11 = pk2(tof(ql[P + 1]), tof(qh[P + 1]));
+    const f2 val = bilerp2(tu, tv, d00, d10, d01, d11);
+    acc[p] = fma2(val, FDK ? mul2(r, mul2(r, WG)) : WG, acc[p]);
+  }
+}
+
 // Views are processed in order; the records of batch k+1 are built at the
 // start of batch k (two record slots), so the footprint of view j+1 is
-// known, and its copy issued, while view j is computed.  Three staging
-// buffers: the copy into buffer (j+1) mod 3 cannot overlap a read of it
-// (view j-2, finished by every thread before the barrier of view j-1), so
-// one barrier per view suffices.
-constexpr int FWD_NBUF = 3;
+// known, and its copy issued, while view j is computed.  With two staging
+// buffers a second barrier per view guards their reuse; with three it is
+// not needed (the copy into buffer (j+1) mod 3 cannot overlap a read of it:
+// view j-2 was finished by every thread before the barrier of view j-1),
+// but the third buffer costs occupancy: two buffers at 4 CTAs/SM measured
+// faster on GB300 than three at 3 CTAs/SM.
+#ifndef BP_FWD_NBUF
+#define BP_FWD_NBUF 2
+#endif
+constexpr int FWD_NBUF = BP_FWD_NBUF;
 
 template <int ZB, typename T, bool FDK, bool STAGE>
 __global__ void __launch_bounds__(NT, FWD_MINB)
@@ -416,10 +502,11 @@ __global__ void __launch_bounds__(NT, FWD_MINB)
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   T* bufs = reinterpret_cast<T*>(dyn_smem);
   constexpr int CAP = STAGE_BYTES / (int)sizeof(T);
+  static_assert(ZB % 2 == 0, "voxel pairs");
   const TileIdx ti = tile_index<ZB>(vi, blockIdx.x);
-  float acc[ZB];
+  f2 acc[ZB / 2];
 #pragma unroll
-  for (int k = 0; k < ZB; ++k) acc[k] = 0.0f;
+  for (int k = 0; k < ZB / 2; ++k) acc[k] = pk2(0.0f, 0.0f);
   const int V = pi.nviews;
   const int nbatch = (V + VB - 1) / VB;
   setup_batch<T, STAGE>(tvs[0], geom, 0, min(VB, V), ti, pi.nu, pi.nv, true);
@@ -448,23 +535,32 @@ __global__ void __launch_bounds__(NT, FWD_MINB)
     __syncthreads();
     if (t.mode != MODE_SKIP) {
       if (STAGE && t.staged) {
-        forward_view_staged<ZB, T, FDK>(bufs + cur * CAP, t, ti.dx, ti.dy, acc);
+        forward_view_staged2<ZB, T, FDK>(bufs + cur * CAP, t, ti.dx, ti.dy, acc);
       } else {
         const T* img = proj + (long long)v * pi.vs;
+        float a[ZB];
+#pragma unroll
+        for (int k = 0; k < ZB / 2; ++k) up2(acc[k], a[2 * k], a[2 * k + 1]);
         if (t.mode == MODE_INTERIOR)
-          forward_view<ZB, T, FDK, false>(img, pi.rs, pi.nu, pi.nv, t, ti.dx, ti.dy, acc);
+          forward_view<ZB, T, FDK, false>(img, pi.rs, pi.nu, pi.nv, t, ti.dx, ti.dy, a);
         else
-          forward_view<ZB, T, FDK, true>(img, pi.rs, pi.nu, pi.nv, t, ti.dx, ti.dy, acc);
+          forward_view<ZB, T, FDK, true>(img, pi.rs, pi.nu, pi.nv, t, ti.dx, ti.dy, a);
+#pragma unroll
+        for (int k = 0; k < ZB / 2; ++k) acc[k] = pk2(a[2 * k], a[2 * k + 1]);
       }
     }
+    if (FWD_NBUF == 2) __syncthreads();
     cur = nxt;
   }
   const int i = ti.tx * TX + ti.lx, j = ti.ty * TY + ti.ly;
   if (i < vi.nx && j < vi.ny) {
 #pragma unroll
-    for (int k = 0; k < ZB; ++k) {
-      const int z = ti.tz * ZB + k;
-      if (z < vi.nz) vol[((long long)z * vi.ny + j) * vi.nx + i] = acc[k];
+    for (int k = 0; k < ZB / 2; ++k) {
+      float lo, hi;
+      up2(acc[k], lo, hi);
+      const int z = ti.tz * ZB + 2 * k;
+      if (z < vi.nz) vol[((long long)z * vi.ny + j) * vi.nx + i] = lo;
+      if (z + 1 < vi.nz) vol[((long long)(z + 1) * vi.ny + j) * vi.nx + i] = hi;
     }
   }
 }
@@ -762,6 +858,96 @@ __device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, const
   }
 }
 
+// The CENTRAL sample loop from a staged central-safe footprint with packed
+// pairs of voxels (k, k+1): the steps of vjp_view in the same order on
+// f32x2 pairs, with the w-component kept negated (na2 = -a2) so that no
+// negation instruction is needed.  Even and odd voxels are summed in the two
+// halves of the pair accumulators and added at the end.
+template <int ZB, typename T, bool FDK, bool EDGE, bool PROJ>
+__device__ __forceinline__ void vjp_view_central2(const T* buf, float* pout, int nu, int nv,
+                                                  const TileView& t, float dx, float dy,
+                                                  const float (&delta)[ZB], float (&S)[3],
+                                                  float (&Z)[3]) {
+  constexpr int P = StageGeom<T>::P;
+  const float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
+  const float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
+  const float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
+  const f2 U0 = pk2(u0, u0), V0 = pk2(v0, v0), W0 = pk2(w0, w0);
+  const f2 RU = pk2(t.ru[2], t.ru[2]), RV = pk2(t.rv[2], t.rv[2]), RW = pk2(t.rw[2], t.rw[2]);
+  const f2 M2 = pk2(MAGIC, MAGIC), TWO = pk2(2.0f, 2.0f), HALF = pk2(0.5f, 0.5f);
+  const f2 WG = pk2(t.wgt, t.wgt);
+  const f2 zero = pk2(0.0f, 0.0f);
+  f2 dz = pk2(-0.5f * (ZB - 1), 1.0f - 0.5f * (ZB - 1));
+  f2 ndz = pk2(0.5f * (ZB - 1), 0.5f * (ZB - 1) - 1.0f);
+  f2 S0 = zero, S1 = zero, S2 = zero, Z0 = zero, Z1 = zero, Z2 = zero;
+#pragma unroll
+  for (int p = 0; p < ZB / 2; ++p) {
+    if (p) {
+      dz = add2(dz, TWO);
+      ndz = sub2(ndz, TWO);
+    }
+    const f2 u = fma2(dz, RU, U0), v = fma2(dz, RV, V0), w = fma2(dz, RW, W0);
+    float wl, wh;
+    up2(w, wl, wh);
+    const f2 r = pk2(rcp_approx(wl), rcp_approx(wh));
+    const f2 x = mul2(u, r), y = mul2(v, r);
+    const f2 rx = add2_rd(x, M2), ry = add2_rd(y, M2);
+    const f2 tu = sub2(x, sub2(rx, M2)), tv = sub2(y, sub2(ry, M2));
+    float bxl, bxh, byl, byh;
+    up2(rx, bxl, bxh);
+    up2(ry, byl, byh);
+    const T* ql = staged_tap(buf, t, __float_as_int(bxl), __float_as_int(byl));
+    const T* qh = staged_tap(buf, t, __float_as_int(bxh), __float_as_int(byh));
+#define BP_TAP2(o) pk2(tof(ql[o]), tof(qh[o]))
+    const f2 a0 = BP_TAP2(-P), a1 = BP_TAP2(-P + 1);
+    const f2 b0 = BP_TAP2(-1), b1 = BP_TAP2(0), b2 = BP_TAP2(1), b3 = BP_TAP2(2);
+    const f2 c0 = BP_TAP2(P - 1), c1 = BP_TAP2(P), c2 = BP_TAP2(P + 1), c3 = BP_TAP2(P + 2);
+    const f2 e0 = BP_TAP2(2 * P), e1 = BP_TAP2(2 * P + 1);
+#undef BP_TAP2
+    // twice the central-difference gradient images at the four tap pixels
+    const f2 gu = bilerp2(tu, tv, sub2(b2, b0), sub2(b3, b1), sub2(c2, c0), sub2(c3, c1));
+    const f2 gv = bilerp2(tu, tv, sub2(c1, a0), sub2(c2, a1), sub2(e0, b1), sub2(e1, b2));
+    const f2 D = pk2(delta[2 * p], delta[2 * p + 1]);
+    const f2 sd = mul2(D, FDK ? mul2(r, mul2(r, WG)) : WG);
+    const f2 sr = mul2(sd, r);
+    const f2 sg = mul2(sr, HALF);
+    const f2 A0 = mul2(gu, sg), A1 = mul2(gv, sg);
+    f2 NA2 = fma2(A0, x, mul2(A1, y));
+    if (FDK) NA2 = fma2(add2(sr, sr), bilerp2(tu, tv, b1, b2, c1, c2), NA2);
+    S0 = add2(S0, A0);
+    S1 = add2(S1, A1);
+    S2 = sub2(S2, NA2);
+    Z0 = fma2(A0, dz, Z0);
+    Z1 = fma2(A1, dz, Z1);
+    Z2 = fma2(NA2, ndz, Z2);
+    if (PROJ) {  // fused data VJP, per voxel: same sample, dequantised weight
+      float rl, rh, tul, tuh, tvl, tvh;
+      up2(r, rl, rh);
+      up2(tu, tul, tuh);
+      up2(tv, tvl, tvh);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 2 * p + h;
+        if (delta[k] == 0.0f) continue;
+        Sample s;
+        const float rk = h ? rh : rl;
+        s.tu = h ? tuh : tul;
+        s.tv = h ? tvh : tvl;
+        s.iu = __float_as_int(h ? bxh : bxl) - MAGIC_BITS + t.au;
+        s.iv = __float_as_int(h ? byh : byl) - MAGIC_BITS + t.av;
+        scatter_sample<EDGE>(pout, nu, nv, s, delta[k] * (FDK ? rk * (rk * t.wgtd) : t.wgtd));
+      }
+    }
+  }
+  float lo, hi;
+  up2(S0, lo, hi); S[0] += lo + hi;
+  up2(S1, lo, hi); S[1] += lo + hi;
+  up2(S2, lo, hi); S[2] += lo + hi;
+  up2(Z0, lo, hi); Z[0] += lo + hi;
+  up2(Z1, lo, hi); Z[1] += lo + hi;
+  up2(Z2, lo, hi); Z[2] += lo + hi;
+}
+
 // One view of one tile: the sample loop (from the staged footprint when it
 // was staged), then the warp reduce-scatter of the 12 sums into red[][b].
 template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ>
@@ -771,7 +957,11 @@ __device__ __forceinline__ void vjp_tile_view(const T* img, const float2* gimg, 
                                               const float (&delta)[ZB],
                                               float (*red)[VB][12], int b) {
   float S[3] = {0.0f, 0.0f, 0.0f}, Z[3] = {0.0f, 0.0f, 0.0f};
-  if (staged) {
+  if (staged && !EXACT) {
+    // CENTRAL footprints are staged only for central-safe, hence interior, tiles
+    vjp_view_central2<ZB, T, FDK, false, PROJ>(buf, pout, pi.nu, pi.nv, t, ti.dx, ti.dy, delta, S,
+                                               Z);
+  } else if (staged) {
     if (t.mode == MODE_INTERIOR || !PROJ)
       vjp_view<ZB, T, FDK, EXACT, false, PROJ, SRC_SMEM>(img, gimg, buf, pout, pi.rs, pi.nu,
                                                          pi.nv, t, ti.dx, ti.dy, delta, S, Z);
