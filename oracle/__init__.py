@@ -1,7 +1,8 @@
 """Oracle: plain FP64 CPU restatement of the paper's backprojection (Eq. 3),
 its analytic Jacobian (Eqs. 4-5), the rigid motion composition (Eq. 1), the
 chain rule (Eq. 2), the gradient-descent update (Eq. 6), Adam, a sharpness
-loss, total variation and the reprojection error (Sec. IV-A).
+loss, total variation, the reprojection error (Sec. IV-A) and the Akima
+spline motion model (Sec. II-B.1).
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package; the product path
@@ -67,6 +68,8 @@ def _load():
                                 ctypes.c_double]
         lib.orc_rpe.restype = ctypes.c_double
         lib.orc_num_threads.restype = ctypes.c_int
+        lib.orc_akima_eval.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, dp, dp]
+        lib.orc_akima_jacobian.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, dp, dp]
         _lib = lib
     return _lib
 
@@ -215,3 +218,48 @@ def rpe(Pa, Pb, pts, du, dv):
     pts = _f64(pts)
     return float(_load().orc_rpe(Pa.shape[0], _ptr(Pa), _ptr(Pb), pts.shape[0], _ptr(pts),
                                  float(du), float(dv)))
+
+
+def akima_eval(y, xe, x=None):
+    """Akima spline through (x_i, y_i) (x defaults to 0..n-1) at points xe."""
+    y = _f64(y)
+    n = y.shape[0]
+    x = _f64(np.arange(n) if x is None else x)
+    xe = _f64(xe)
+    out = np.zeros(xe.shape[0])
+    _load().orc_akima_eval(n, _ptr(x), _ptr(y), xe.shape[0], _ptr(xe), _ptr(out))
+    return out
+
+
+def akima_jacobian(y, xe, x=None):
+    """d spline(xe_q) / d y_k, shape (len(xe), n), by forward-mode duals."""
+    y = _f64(y)
+    n = y.shape[0]
+    x = _f64(np.arange(n) if x is None else x)
+    xe = _f64(xe)
+    J = np.zeros((xe.shape[0], n))
+    _load().orc_akima_jacobian(n, _ptr(x), _ptr(y), xe.shape[0], _ptr(xe), _ptr(J))
+    return J
+
+
+def motion_knots(n_nodes, nviews):
+    """Knots of the motion splines: evenly spread over the view index, one at
+    the first view and one at the last (Sec. II-B.1)."""
+    return np.linspace(0.0, nviews - 1.0, n_nodes)
+
+
+def akima_motion(nodes, nviews):
+    """theta (V,6): the six splines through nodes (N_n,6) at views 0..V-1."""
+    nodes = _f64(nodes)
+    x = motion_knots(nodes.shape[0], nviews)
+    xe = np.arange(nviews, dtype=np.float64)
+    return np.stack([akima_eval(nodes[:, p], xe, x) for p in range(6)], axis=1)
+
+
+def akima_motion_vjp(nodes, nviews, dL_dtheta):
+    """dL/dnodes (N_n,6) = J^T dL/dtheta per parameter, J from akima_jacobian."""
+    nodes = _f64(nodes)
+    g = _f64(dL_dtheta)
+    x = motion_knots(nodes.shape[0], nviews)
+    xe = np.arange(nviews, dtype=np.float64)
+    return np.stack([akima_jacobian(nodes[:, p], xe, x).T @ g[:, p] for p in range(6)], axis=1)

@@ -449,3 +449,109 @@ int orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------
+ * Akima spline motion model (Sec. II-B.1): each of the six motion
+ * parameters is an Akima spline through N_n node values at knots spread
+ * evenly over the scan, first knot at the first view and last knot at the
+ * last; theta_j is the splines evaluated at view j's time.
+ *
+ * Akima's construction, in the order it is defined:
+ *   secants      m_i = (y_{i+1} - y_i) / (x_{i+1} - x_i),     i = 0 .. n-2
+ *   end secants  two more at each end by linear extrapolation of the
+ *                secant sequence: m_{-1} = 2 m_0 - m_1, m_{-2} = 2 m_{-1} - m_0,
+ *                m_{n-1} = 2 m_{n-2} - m_{n-3}, m_n = 2 m_{n-1} - m_{n-2}
+ *   node slopes  t_i = (|m_{i+1} - m_i| m_{i-1} + |m_{i-1} - m_{i-2}| m_i)
+ *                      / (|m_{i+1} - m_i| + |m_{i-1} - m_{i-2}|),
+ *                and (m_{i-1} + m_i) / 2 where the denominator is 0
+ *   pieces       the cubic Hermite interpolant of (y_i, t_i), (y_{i+1}, t_{i+1})
+ *                on [x_i, x_{i+1}].
+ * Needs n >= 3.
+ *
+ * Every quantity is carried as a dual number (value, derivative along one
+ * direction dy of the node values), so one pass also gives one column of
+ * the Jacobian d(spline values)/d(node values): forward-mode
+ * differentiation written out, independent of any reverse-mode code.
+ * ---------------------------------------------------------------------- */
+typedef struct { double v, d; } orc_dual;
+
+static orc_dual dl_add(orc_dual a, orc_dual b) { orc_dual r = {a.v + b.v, a.d + b.d}; return r; }
+static orc_dual dl_sub(orc_dual a, orc_dual b) { orc_dual r = {a.v - b.v, a.d - b.d}; return r; }
+static orc_dual dl_scale(double s, orc_dual a) { orc_dual r = {s * a.v, s * a.d}; return r; }
+static orc_dual dl_mul(orc_dual a, orc_dual b) {
+  orc_dual r = {a.v * b.v, a.d * b.v + a.v * b.d};
+  return r;
+}
+static orc_dual dl_div(orc_dual a, orc_dual b) {
+  orc_dual r = {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)};
+  return r;
+}
+static orc_dual dl_abs(orc_dual a) {
+  const double s = a.v > 0.0 ? 1.0 : (a.v < 0.0 ? -1.0 : 0.0);
+  orc_dual r = {fabs(a.v), s * a.d};
+  return r;
+}
+
+/* Values (and derivatives along dy, which may be NULL for zero) of the
+ * spline through (x_i, y_i), i < n, at the m points xe; n >= 3. */
+static void akima_dual(int n, const double* x, const double* y, const double* dy, int m,
+                       const double* xe, double* out, double* dout) {
+  orc_dual* s = (orc_dual*)malloc(sizeof(orc_dual) * (size_t)(n + 3)); /* s[k] = m_{k-2} */
+  orc_dual* t = (orc_dual*)malloc(sizeof(orc_dual) * (size_t)n);
+  for (int i = 0; i + 1 < n; ++i) {
+    const orc_dual a = {y[i], dy ? dy[i] : 0.0}, b = {y[i + 1], dy ? dy[i + 1] : 0.0};
+    s[i + 2] = dl_scale(1.0 / (x[i + 1] - x[i]), dl_sub(b, a));
+  }
+  s[1] = dl_sub(dl_scale(2.0, s[2]), s[3]);
+  s[0] = dl_sub(dl_scale(2.0, s[1]), s[2]);
+  s[n + 1] = dl_sub(dl_scale(2.0, s[n]), s[n - 1]);
+  s[n + 2] = dl_sub(dl_scale(2.0, s[n + 1]), s[n]);
+  for (int i = 0; i < n; ++i) {
+    /* m_{i-2} = s[i], m_{i-1} = s[i+1], m_i = s[i+2], m_{i+1} = s[i+3] */
+    const orc_dual w1 = dl_abs(dl_sub(s[i + 3], s[i + 2]));
+    const orc_dual w2 = dl_abs(dl_sub(s[i + 1], s[i]));
+    const orc_dual den = dl_add(w1, w2);
+    if (den.v == 0.0)
+      t[i] = dl_scale(0.5, dl_add(s[i + 1], s[i + 2]));
+    else
+      t[i] = dl_div(dl_add(dl_mul(w1, s[i + 1]), dl_mul(w2, s[i + 2])), den);
+  }
+  for (int q = 0; q < m; ++q) {
+    int i = 0;
+    while (i < n - 2 && xe[q] >= x[i + 1]) ++i;
+    const double h = x[i + 1] - x[i], e = xe[q] - x[i];
+    const orc_dual yi = {y[i], dy ? dy[i] : 0.0};
+    const orc_dual mi = s[i + 2];
+    /* p = y_i + t_i e + c e^2 + d e^3 with c = (3 m_i - 2 t_i - t_{i+1}) / h,
+       d = (t_i + t_{i+1} - 2 m_i) / h^2 */
+    const orc_dual c = dl_scale(1.0 / h, dl_sub(dl_sub(dl_scale(3.0, mi), dl_scale(2.0, t[i])), t[i + 1]));
+    const orc_dual d = dl_scale(1.0 / (h * h), dl_sub(dl_add(t[i], t[i + 1]), dl_scale(2.0, mi)));
+    const orc_dual p = dl_add(dl_add(yi, dl_scale(e, t[i])), dl_add(dl_scale(e * e, c), dl_scale(e * e * e, d)));
+    out[q] = p.v;
+    if (dout) dout[q] = p.d;
+  }
+  free(s);
+  free(t);
+}
+
+/* Spline values at xe (m points) through n >= 3 knots (x, y). */
+void orc_akima_eval(int n, const double* x, const double* y, int m, const double* xe, double* out) {
+  akima_dual(n, x, y, NULL, m, xe, out, NULL);
+}
+
+/* Jacobian J[q][k] = d spline(xe_q) / d y_k, m x n, by forward-mode duals. */
+void orc_akima_jacobian(int n, const double* x, const double* y, int m, const double* xe,
+                        double* J) {
+  double* dy = (double*)calloc((size_t)n, sizeof(double));
+  double* out = (double*)malloc(sizeof(double) * (size_t)m);
+  double* dout = (double*)malloc(sizeof(double) * (size_t)m);
+  for (int k = 0; k < n; ++k) {
+    dy[k] = 1.0;
+    akima_dual(n, x, y, dy, m, xe, out, dout);
+    for (int q = 0; q < m; ++q) J[(size_t)q * n + k] = dout[q];
+    dy[k] = 0.0;
+  }
+  free(dy);
+  free(out);
+  free(dout);
+}
