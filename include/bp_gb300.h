@@ -202,6 +202,25 @@ int bp_adam_step(bp_ctx* ctx, int nviews, double* theta, const double* grad, dou
                  double* m2, double lr, double beta1, double beta2, double eps, int n, int gauge,
                  void* stream);
 
+/* Akima spline motion model (Sec. II-B.1): each of the six motion parameters
+ * is an Akima spline through n_nodes node values at knots spread evenly over
+ * the views (first knot at view 0, last at view nviews-1), and theta[j] is
+ * the six splines at view j.  Akima's construction: secants between nodes,
+ * two more secants per end by linear extrapolation, node slopes as the
+ * |secant difference|-weighted mean of the two neighbouring secants (their
+ * plain mean where both weights are 0), cubic Hermite pieces.
+ *   nodes       float64 [n_nodes][6] (same parameter order as theta);
+ *   theta       float64 [nviews][6] output;
+ *   dL_dtheta   float64 [nviews][6]; dL_dnodes float64 [n_nodes][6] output
+ *               = (d theta / d nodes)^T dL_dtheta, per parameter.
+ * Requires 3 <= n_nodes <= 512 and nviews >= 2 (BP_ERR_INVALID_ARG or
+ * BP_ERR_UNSUPPORTED otherwise).  FP64 throughout; arrays host or device.
+ * The VJP sums in a fixed order (deterministic). */
+int bp_akima_motion(bp_ctx* ctx, int n_nodes, int nviews, const double* nodes, double* theta,
+                    void* stream);
+int bp_akima_motion_vjp(bp_ctx* ctx, int n_nodes, int nviews, const double* nodes,
+                        const double* dL_dtheta, double* dL_dnodes, void* stream);
+
 /* ------------------------------------------------------------------ jobs
  * A motion-estimation job (Sec. II-C): everything one scan needs stays on the
  * device -- projections, gradient images, theta, optimiser state, volume and
@@ -222,12 +241,17 @@ typedef struct {
   int gauge;        /* remove the per-parameter view mean after each step */
   int loss;         /* bp_loss: the image-quality target minimised */
   double tv_eps;    /* eps of BP_LOSS_TV */
+  int motion_nodes; /* 0: one free theta per view (6V parameters); 3..512: the
+                       Akima spline motion model of Sec. II-B.1 (bp_akima_motion)
+                       with this many nodes, and the optimiser works on the
+                       6 N_n node values (gauge: mean over nodes removed) */
 } bp_opt_desc;
 
 typedef struct bp_job bp_job;
 
 /* Create a job: copies proj (any location; stored compactly in its dtype), P,
- * view_weight and theta0 (NULL = zero motion) to job-owned device memory and
+ * view_weight and theta0 (NULL = zero motion; [V][6] per-view values, or
+ * [N_n][6] node values when opt->motion_nodes > 0) to job-owned device memory and
  * precomputes the gradient images (CENTRAL).  max_iters bounds the loss
  * history.  Admission: if the job's device bytes (bp_job_bytes) would take
  * the context's live jobs beyond its HBM budget (bp_ctx_set_hbm_budget, or the
@@ -246,11 +270,15 @@ int bp_ctx_set_hbm_budget(bp_ctx* ctx, long long bytes);
  * job-owned stream.  Jobs on different streams overlap on the device. */
 int motion_step(bp_job* job, int n_iters, void* stream);
 /* Wait for the job's queued iterations (not for other work on the device)
- * and copy theta (float64 [V][6]) and the loss history (float64
+ * and copy theta (float64 [V][6]; with the spline model, the splines of the
+ * current nodes at every view) and the loss history (float64
  * [max_iters], may be NULL) to host memory; *iters_done (may be NULL)
  * receives the number of iterations run. */
 int bp_job_get_motion(const bp_job* job, double* theta_host, double* loss_history,
                       int* iters_done);
+/* Copy the current spline node values (float64 [N_n][6]) of a job with the
+ * Akima motion model to host memory (BP_ERR_INVALID_ARG for per-view jobs). */
+int bp_job_get_nodes(const bp_job* job, double* nodes_host);
 /* The job's current volume (float32, device pointer owned by the job). */
 const float* bp_job_volume(const bp_job* job);
 /* Waits for the job's queued iterations, then frees its memory with the

@@ -47,3 +47,23 @@ def backproject(proj, motion, P, *, vol_shape, spacing, origin, sid, view_weight
     """Differentiable w.r.t. proj (V,nv,nu) and motion (V,6) float64."""
     return _Backproject.apply(proj, motion, P, tuple(vol_shape), tuple(spacing), tuple(origin),
                               float(sid), view_weight, weight, deriv)
+
+
+class _AkimaMotion(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, nodes, nviews):
+        ctx.save_for_backward(nodes)
+        return bp.bp_akima_motion(nodes.contiguous(), nviews)
+
+    @staticmethod
+    def backward(ctx, gtheta):
+        (nodes,) = ctx.saved_tensors
+        return bp.bp_akima_motion_vjp(nodes.contiguous(), gtheta.contiguous()), None
+
+
+def akima_motion(nodes, nviews):
+    """Motion model of Sec. II-B.1 as a differentiable function: per-view
+    theta (V,6) from Akima spline node values (N_n,6), float64.  Chain it into
+    `backproject` to optimise the 6 N_n node values instead of 6 V
+    per-view parameters."""
+    return _AkimaMotion.apply(nodes, int(nviews))

@@ -114,6 +114,31 @@ def bp_tv(vol, eps=1e-3, want_grad=True, loss_out=None, grad_out=None):
     return loss, grad
 
 
+def bp_akima_motion(nodes, nviews, out=None):
+    """Sec. II-B.1: theta (V,6) float64 from Akima spline nodes (N_n,6)."""
+    nodes = _f64(nodes, "nodes")
+    if out is None:
+        out = torch.empty((nviews, 6), dtype=torch.float64, device=nodes.device)
+    ctx = N.context(N.device_of(nodes, out))
+    rc = N.lib().bp_akima_motion(ctx, nodes.shape[0], int(nviews), N.ptr(nodes), N.ptr(out),
+                                 N.stream_of(nodes, out))
+    N.check("bp_akima_motion", rc, ctx)
+    return out
+
+
+def bp_akima_motion_vjp(nodes, dL_dtheta, out=None):
+    """dL/dnodes (N_n,6) = (dtheta/dnodes)^T dL/dtheta for the Akima motion model."""
+    nodes = _f64(nodes, "nodes")
+    g = _f64(dL_dtheta, "dL_dtheta")
+    if out is None:
+        out = torch.empty_like(nodes)
+    ctx = N.context(N.device_of(nodes, g, out))
+    rc = N.lib().bp_akima_motion_vjp(ctx, nodes.shape[0], g.shape[0], N.ptr(nodes), N.ptr(g),
+                                     N.ptr(out), N.stream_of(nodes, g, out))
+    N.check("bp_akima_motion_vjp", rc, ctx)
+    return out
+
+
 def bp_gd_step(theta, grad, s0, t, n, gauge=True):
     """Eq. 6 step n in place on theta (V,6) float64."""
     ctx = N.context(N.device_of(theta))

@@ -135,7 +135,8 @@ void bp_ctx_destroy(bp_ctx* ctx) {
   Buf* bufs[] = {&ctx->geom,   &ctx->grad,   &ctx->partials,   &ctx->shblk,      &ctx->s_proj,
                  &ctx->s_P,    &ctx->s_motion, &ctx->s_vw,     &ctx->s_scale,    &ctx->s_vol,
                  &ctx->s_dvol, &ctx->s_out_motion, &ctx->s_out_P, &ctx->s_out_proj,
-                 &ctx->s_theta, &ctx->s_grad, &ctx->s_m1,       &ctx->s_m2,       &ctx->s_loss};
+                 &ctx->s_theta, &ctx->s_grad, &ctx->s_m1,       &ctx->s_m2,       &ctx->s_loss,
+                 &ctx->s_nodes, &ctx->s_out_nodes};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   resolve_timing(ctx);
@@ -150,7 +151,8 @@ long long bp_ctx_workspace_bytes(const bp_ctx* ctx) {
   const Buf* bufs[] = {&ctx->geom,   &ctx->grad,   &ctx->partials,   &ctx->shblk,      &ctx->s_proj,
                        &ctx->s_P,    &ctx->s_motion, &ctx->s_vw,     &ctx->s_scale,    &ctx->s_vol,
                        &ctx->s_dvol, &ctx->s_out_motion, &ctx->s_out_P, &ctx->s_out_proj,
-                       &ctx->s_theta, &ctx->s_grad, &ctx->s_m1,       &ctx->s_m2,       &ctx->s_loss};
+                       &ctx->s_theta, &ctx->s_grad, &ctx->s_m1,       &ctx->s_m2,       &ctx->s_loss,
+                       &ctx->s_nodes, &ctx->s_out_nodes};
   long long t = 0;
   for (const Buf* b : bufs) t += (long long)b->n;
   return t;
@@ -481,6 +483,66 @@ int bp_adam_step(bp_ctx* ctx, int nviews, double* theta, const double* grad, dou
                     return TL(K_OPT, 1, bpk::launch_adam(nviews, th, gr, a, b, lr, beta1, beta2, eps, n,
                                                          gauge, s));
                   });
+}
+
+static int check_spline(bp_ctx* ctx, int n_nodes, int nviews) {
+  if (n_nodes < 3 || nviews < 2)
+    return fail(ctx, BP_ERR_INVALID_ARG, "Akima motion: need n_nodes >= 3 and nviews >= 2");
+  if (n_nodes > bpk::AKIMA_MAX_NODES)
+    return fail(ctx, BP_ERR_UNSUPPORTED, "Akima motion: more than 512 nodes");
+  return BP_OK;
+}
+
+int bp_akima_motion(bp_ctx* ctx, int n_nodes, int nviews, const double* nodes, double* theta,
+                    void* stream) {
+  if (!ctx) return BP_ERR_INVALID_ARG;
+  ctx->err.clear();
+  int st = check_spline(ctx, n_nodes, nviews);
+  if (st) return st;
+  if (!nodes || !theta) return fail(ctx, BP_ERR_INVALID_ARG, "bp_akima_motion: NULL array");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const void* q;
+  CK(stage_in(ctx->s_nodes, nodes, sizeof(double) * 6 * n_nodes, s, &q), "copy nodes");
+  void* o;
+  bool host;
+  CK(stage_out(ctx->s_out_motion, theta, sizeof(double) * 6 * nviews, &o, &host), "alloc theta");
+  CK(TL(K_SPLINE, 1, bpk::launch_akima_eval(n_nodes, nviews, (const double*)q, (double*)o, s)),
+     "akima");
+  if (host) {
+    CK(cudaMemcpyAsync(theta, o, sizeof(double) * 6 * nviews, cudaMemcpyDeviceToHost, s),
+       "copy theta");
+    CK(cudaStreamSynchronize(s), "sync");
+  }
+  return BP_OK;
+}
+
+int bp_akima_motion_vjp(bp_ctx* ctx, int n_nodes, int nviews, const double* nodes,
+                        const double* dL_dtheta, double* dL_dnodes, void* stream) {
+  if (!ctx) return BP_ERR_INVALID_ARG;
+  ctx->err.clear();
+  int st = check_spline(ctx, n_nodes, nviews);
+  if (st) return st;
+  if (!nodes || !dL_dtheta || !dL_dnodes)
+    return fail(ctx, BP_ERR_INVALID_ARG, "bp_akima_motion_vjp: NULL array");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const void* q;
+  CK(stage_in(ctx->s_nodes, nodes, sizeof(double) * 6 * n_nodes, s, &q), "copy nodes");
+  const double* dn = (const double*)q;
+  CK(stage_in(ctx->s_grad, dL_dtheta, sizeof(double) * 6 * nviews, s, &q), "copy dL/dtheta");
+  void* o;
+  bool host;
+  CK(stage_out(ctx->s_out_nodes, dL_dnodes, sizeof(double) * 6 * n_nodes, &o, &host),
+     "alloc dL/dnodes");
+  CK(TL(K_SPLINE, 1, bpk::launch_akima_vjp(n_nodes, nviews, dn, (const double*)q, (double*)o, s)),
+     "akima vjp");
+  if (host) {
+    CK(cudaMemcpyAsync(dL_dnodes, o, sizeof(double) * 6 * n_nodes, cudaMemcpyDeviceToHost, s),
+       "copy dL/dnodes");
+    CK(cudaStreamSynchronize(s), "sync");
+  }
+  return BP_OK;
 }
 
 }  // extern "C"

@@ -138,4 +138,11 @@ cudaError_t launch_adam_dev(int V, double* theta, const double* grad, double* m1
 cudaError_t launch_gd_dev(int V, double* theta, const double* grad, double s0_t, double s0_r,
                           double t, int* iter, int gauge, cudaStream_t s);
 
+// Akima spline motion model (bp_spline.cu): nodes [n][6] -> theta [V][6]
+// and its VJP; n >= 3, V >= 2, n <= AKIMA_MAX_NODES.
+constexpr int AKIMA_MAX_NODES = 512;  // VJP shared memory: 8 (8n + 2) bytes
+cudaError_t launch_akima_eval(int n, int V, const double* nodes, double* theta, cudaStream_t s);
+cudaError_t launch_akima_vjp(int n, int V, const double* nodes, const double* g, double* dnodes,
+                             cudaStream_t s);
+
 }  // namespace bpk

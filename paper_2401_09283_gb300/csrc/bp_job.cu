@@ -21,6 +21,8 @@ struct bp_job {
   float* scale = nullptr;
   double *P = nullptr, *vw = nullptr, *theta = nullptr, *m1 = nullptr, *m2 = nullptr,
          *gth = nullptr, *blk = nullptr, *hist = nullptr;
+  int nodes = 0;                               // Akima motion model: N_n (0: per view)
+  double *x = nullptr, *gx = nullptr;          // node values and their gradient [N_n][6]
   bpk::ViewGeom* geom = nullptr;
   float2* grad = nullptr;
   float *partials = nullptr, *vol = nullptr, *dvol = nullptr;
@@ -42,8 +44,8 @@ long long align_up(long long x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // The job's buffers in allocation order (sizes in bytes).
 struct Layout {
-  long long proj, scale, P, vw, theta, m1, m2, gth, geom, grad, partials, vol, dvol, blk, hist,
-      iter, total;
+  long long proj, scale, P, vw, theta, m1, m2, gth, x, gx, geom, grad, partials, vol, dvol, blk,
+      hist, iter, total;
 };
 
 Layout layout(const bp_proj_desc* pd, const bp_vol_desc* vd, int deriv, int max_iters) {
@@ -55,7 +57,12 @@ Layout layout(const bp_proj_desc* pd, const bp_vol_desc* vd, int deriv, int max_
   L.scale = align_up(V * 4);
   L.P = align_up(V * 96);
   L.vw = align_up(V * 8);
-  L.theta = L.m1 = L.m2 = L.gth = align_up(V * 48);
+  L.theta = L.gth = align_up(V * 48);
+  // optimiser state holds either V per-view rows or up to AKIMA_MAX_NODES
+  // node rows; node buffers are always reserved, so the size does not
+  // depend on the motion model
+  L.m1 = L.m2 = align_up((V > bpk::AKIMA_MAX_NODES ? V : bpk::AKIMA_MAX_NODES) * 48LL);
+  L.x = L.gx = align_up(bpk::AKIMA_MAX_NODES * 48LL);
   L.geom = align_up(V * (long long)sizeof(bpk::ViewGeom));
   L.grad = deriv == BP_DERIV_CENTRAL ? align_up(V * npx * 8) : 0;
   L.partials = align_up(V * tiles * bpk::PSLOTS * 4);
@@ -63,8 +70,8 @@ Layout layout(const bp_proj_desc* pd, const bp_vol_desc* vd, int deriv, int max_
   L.blk = align_up(bpk::sharpness_blocks(nvox) * 8LL);
   L.hist = align_up((long long)max_iters * 8);
   L.iter = kAlign;
-  L.total = L.proj + L.scale + L.P + L.vw + 4 * L.theta + L.geom + L.grad + L.partials +
-            2 * L.vol + L.blk + L.hist + L.iter;
+  L.total = L.proj + L.scale + L.P + L.vw + L.theta + L.gth + L.m1 + L.m2 + L.x + L.gx + L.geom +
+            L.grad + L.partials + 2 * L.vol + L.blk + L.hist + L.iter;
   return L;
 }
 
@@ -92,6 +99,10 @@ cudaError_t record_iteration(bp_job* j, cudaStream_t s) {
   const int fdk = j->weight == BP_WEIGHT_FDK;
   const int V = j->pd.nviews;
   cudaError_t e;
+  if (j->nodes) {
+    e = bpk::launch_akima_eval(j->nodes, V, j->x, j->theta, s);
+    if (e != cudaSuccess) return e;
+  }
   e = bpk::launch_compose(j->P, j->theta, j->vw, j->scale, V, fdk, j->pd.sid, j->vi, j->geom,
                           nullptr, s);
   if (e != cudaSuccess) return e;
@@ -110,14 +121,25 @@ cudaError_t record_iteration(bp_job* j, cudaStream_t s) {
   e = bpk::launch_reduce_chain(j->partials, j->ntiles, j->vi, j->P, j->theta, V, nullptr, j->gth,
                                s);
   if (e != cudaSuccess) return e;
+  // the optimiser's variables: per-view theta, or the spline nodes
+  int rows = V;
+  double *var = j->theta, *grad = j->gth;
+  if (j->nodes) {
+    e = bpk::launch_akima_vjp(j->nodes, V, j->x, j->gth, j->gx, s);
+    if (e != cudaSuccess) return e;
+    rows = j->nodes;
+    var = j->x;
+    grad = j->gx;
+  }
   if (j->opt.optimizer == BP_OPT_ADAM)
-    return bpk::launch_adam_dev(V, j->theta, j->gth, j->m1, j->m2, j->opt.lr, j->opt.lr_rot,
+    return bpk::launch_adam_dev(rows, var, grad, j->m1, j->m2, j->opt.lr, j->opt.lr_rot,
                                 j->opt.beta1, j->opt.beta2, j->opt.eps, j->iter, j->opt.gauge, s);
-  return bpk::launch_gd_dev(V, j->theta, j->gth, j->opt.lr, j->opt.lr_rot, j->opt.decay, j->iter,
+  return bpk::launch_gd_dev(rows, var, grad, j->opt.lr, j->opt.lr_rot, j->opt.decay, j->iter,
                             j->opt.gauge, s);
 }
 
-constexpr int kKernelsPerIteration = 7;  // compose, forward, 2 loss, VJP, reduce, update
+// compose, forward, 2 loss, VJP, reduce, update (+ spline and its VJP)
+int kernels_per_iteration(const bp_job* j) { return j->nodes ? 9 : 7; }
 
 }  // namespace
 
@@ -158,6 +180,10 @@ int bp_job_create(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, cons
       (opt->loss != BP_LOSS_SHARPNESS && opt->loss != BP_LOSS_TV) ||
       (opt->loss == BP_LOSS_TV && !(opt->tv_eps > 0.0)))
     return fail(ctx, BP_ERR_INVALID_ARG, "bp_job_create: unknown weight/deriv/optimizer/loss");
+  if (opt->motion_nodes != 0 &&
+      (opt->motion_nodes < 3 || opt->motion_nodes > bpk::AKIMA_MAX_NODES || pdesc->nviews < 2))
+    return fail(ctx, BP_ERR_INVALID_ARG,
+                "bp_job_create: motion_nodes must be 0 or 3..512 (with >= 2 views)");
   DeviceGuard g(ctx->device);
   const Layout L = layout(pdesc, vdesc, deriv, max_iters);
   // admission by device memory
@@ -206,6 +232,9 @@ int bp_job_create(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, cons
   j->m1 = (double*)take(L.m1);
   j->m2 = (double*)take(L.m2);
   j->gth = (double*)take(L.gth);
+  j->x = (double*)take(L.x);
+  j->gx = (double*)take(L.gx);
+  j->nodes = opt->motion_nodes;
   j->geom = (bpk::ViewGeom*)take(L.geom);
   j->grad = L.grad ? (float2*)take(L.grad) : nullptr;
   j->partials = (float*)take(L.partials);
@@ -238,11 +267,14 @@ int bp_job_create(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, cons
     else j->scale = nullptr;
   }
   if (e == cudaSuccess) {
-    if (theta0) e = cudaMemcpyAsync(j->theta, theta0, 48 * (size_t)V, cudaMemcpyDefault, os);
-    else e = cudaMemsetAsync(j->theta, 0, 48 * (size_t)V, os);
+    double* init = j->nodes ? j->x : j->theta;
+    const size_t rows = j->nodes ? (size_t)j->nodes : (size_t)V;
+    if (theta0) e = cudaMemcpyAsync(init, theta0, 48 * rows, cudaMemcpyDefault, os);
+    else e = cudaMemsetAsync(init, 0, 48 * rows, os);
+    if (e == cudaSuccess && j->nodes) e = cudaMemsetAsync(j->theta, 0, 48 * (size_t)V, os);
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(j->m1, 0, 48 * (size_t)V, os);
-  if (e == cudaSuccess) e = cudaMemsetAsync(j->m2, 0, 48 * (size_t)V, os);
+  if (e == cudaSuccess) e = cudaMemsetAsync(j->m1, 0, (size_t)L.m1, os);
+  if (e == cudaSuccess) e = cudaMemsetAsync(j->m2, 0, (size_t)L.m2, os);
   if (e == cudaSuccess) e = cudaMemsetAsync(j->iter, 0, sizeof(int), os);
   if (e == cudaSuccess && max_iters > 0) e = cudaMemsetAsync(j->hist, 0, 8 * (size_t)max_iters, os);
   j->pd.row_stride = pdesc->nu;
@@ -319,7 +351,7 @@ int motion_step(bp_job* j, int n_iters, void* stream) {
     e = cudaGraphLaunch(j->exec, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "motion_step: launch");
   }
-  ctx->launches += (long long)kKernelsPerIteration * n_iters;
+  ctx->launches += (long long)kernels_per_iteration(j) * n_iters;
   e = cudaEventRecord(j->done, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "motion_step: record");
   return BP_OK;
@@ -333,6 +365,8 @@ int bp_job_get_motion(const bp_job* j, double* theta_host, double* loss_history,
   // device-wide synchronisation, so other jobs keep running
   cudaStream_t os = j->own;
   cudaError_t e = cudaStreamWaitEvent(os, j->done, 0);
+  if (e == cudaSuccess && theta_host && j->nodes)  // theta of the current nodes
+    e = bpk::launch_akima_eval(j->nodes, j->pd.nviews, j->x, j->theta, os);
   if (e == cudaSuccess && theta_host)
     e = cudaMemcpyAsync(theta_host, j->theta, 48 * (size_t)j->pd.nviews, cudaMemcpyDeviceToHost, os);
   if (e == cudaSuccess && loss_history && j->max_iters > 0)
@@ -341,6 +375,19 @@ int bp_job_get_motion(const bp_job* j, double* theta_host, double* loss_history,
     e = cudaMemcpyAsync(iters_done, j->iter, sizeof(int), cudaMemcpyDeviceToHost, os);
   if (e == cudaSuccess) e = cudaStreamSynchronize(os);
   if (e != cudaSuccess) return cuda_fail(j->ctx, e, "bp_job_get_motion");
+  return BP_OK;
+}
+
+int bp_job_get_nodes(const bp_job* j, double* nodes_host) {
+  if (!j || !nodes_host) return BP_ERR_INVALID_ARG;
+  if (!j->nodes) return fail(j->ctx, BP_ERR_INVALID_ARG, "bp_job_get_nodes: per-view job");
+  DeviceGuard g(j->device);
+  cudaStream_t os = j->own;
+  cudaError_t e = cudaStreamWaitEvent(os, j->done, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(nodes_host, j->x, 48 * (size_t)j->nodes, cudaMemcpyDeviceToHost, os);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(os);
+  if (e != cudaSuccess) return cuda_fail(j->ctx, e, "bp_job_get_nodes");
   return BP_OK;
 }
 

@@ -957,8 +957,10 @@ __device__ __forceinline__ void vjp_tile_view(const T* img, const float2* gimg, 
                                               const float (&delta)[ZB],
                                               float (*red)[VB][12], int b) {
   float S[3] = {0.0f, 0.0f, 0.0f}, Z[3] = {0.0f, 0.0f, 0.0f};
-  if (staged && !EXACT) {
-    // CENTRAL footprints are staged only for central-safe, hence interior, tiles
+  if (staged && !EXACT && !PROJ) {
+    // CENTRAL footprints are staged only for central-safe, hence interior,
+    // tiles.  (With the fused data VJP the per-voxel scatter needs the
+    // samples unpacked, and the scalar loop measured faster there.)
     vjp_view_central2<ZB, T, FDK, false, PROJ>(buf, pout, pi.nu, pi.nv, t, ti.dx, ti.dy, delta, S,
                                                Z);
   } else if (staged) {

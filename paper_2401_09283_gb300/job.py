@@ -3,7 +3,9 @@
 A job owns device copies of the projections and all optimiser state;
 motion_step() replays one captured CUDA graph per iteration (compose ->
 backprojection -> sharpness loss -> motion VJP -> FP64 reduction and chain
-rule -> Adam or the decaying gradient step of Eq. 6)."""
+rule -> Adam or the decaying gradient step of Eq. 6).  With motion_nodes > 0
+the motion is the Akima spline model of Sec. II-B.1 and the optimiser works
+on the 6 N_n node values (spline and spline VJP run inside the graph)."""
 from __future__ import annotations
 
 import ctypes
@@ -21,8 +23,10 @@ class MotionJob:
     def __init__(self, proj, P, *, vol_shape, spacing, origin, sid, view_weight=None,
                  weight="fdk", deriv="central", optimizer="adam", lr=0.1, lr_rot=1e-3,
                  decay=0.97, betas=(0.9, 0.999), eps=1e-8, gauge=True, theta0=None,
-                 max_iters=100, view_scale=None, device=None, loss="sharpness", tv_eps=1e-3):
+                 max_iters=100, view_scale=None, device=None, loss="sharpness", tv_eps=1e-3,
+                 motion_nodes=0):
         self.V = int(P.shape[0])
+        self.nodes = int(motion_nodes)
         self.max_iters = int(max_iters)
         if device is None:
             device = N.device_of(proj, P)
@@ -31,7 +35,8 @@ class MotionJob:
         pd = N.proj_desc(proj, sid, view_scale)
         vd = N.vol_desc(vol_shape, spacing, origin)
         od = N.OptDesc(OPT[optimizer], float(lr), float(lr_rot), float(decay), float(betas[0]),
-                       float(betas[1]), float(eps), int(bool(gauge)), LOSS[loss], float(tv_eps))
+                       float(betas[1]), float(eps), int(bool(gauge)), LOSS[loss], float(tv_eps),
+                       self.nodes)
         Pc = P if isinstance(P, torch.Tensor) else torch.as_tensor(np.ascontiguousarray(P))
         self._keep = (proj, Pc, view_weight, theta0, view_scale)
         h = ctypes.c_void_p()
@@ -71,6 +76,13 @@ class MotionJob:
                                        ctypes.byref(it))
         N.check("bp_job_get_motion", rc, self.ctx)
         return th, hist[: self.max_iters], int(it.value)
+
+    def node_values(self):
+        """Current spline node values (N_n,6) of a job with the Akima model."""
+        x = np.zeros((self.nodes, 6))
+        rc = N.lib().bp_job_get_nodes(self.handle, x.ctypes.data)
+        N.check("bp_job_get_nodes", rc, self.ctx)
+        return x
 
     def close(self):
         if getattr(self, "handle", None):

@@ -40,7 +40,7 @@ class ProjDesc(ctypes.Structure):
 class OptDesc(ctypes.Structure):
     _fields_ = [("optimizer", c_int), ("lr", c_double), ("lr_rot", c_double), ("decay", c_double),
                 ("beta1", c_double), ("beta2", c_double), ("eps", c_double), ("gauge", c_int),
-                ("loss", c_int), ("tv_eps", c_double)]
+                ("loss", c_int), ("tv_eps", c_double), ("motion_nodes", c_int)]
 
 
 class BPError(RuntimeError):
@@ -58,7 +58,7 @@ EXPORTS = ["bp_ctx_create", "bp_ctx_destroy", "bp_last_error", "bp_ctx_workspace
            "bp_compose", "bp_forward", "bp_vjp", "bp_sharpness", "bp_tv", "bp_sharpness_noalloc",
            "bp_gd_step", "bp_adam_step", "bp_job_create", "bp_job_bytes_for", "bp_job_bytes",
            "bp_ctx_set_hbm_budget", "motion_step", "bp_job_get_motion", "bp_job_volume",
-           "bp_job_destroy"]
+           "bp_job_destroy", "bp_akima_motion", "bp_akima_motion_vjp", "bp_job_get_nodes"]
 
 
 def lib():
@@ -112,6 +112,9 @@ def lib():
                 L.bp_job_volume.restype = c_void_p
                 L.bp_job_destroy.argtypes = [vp]
                 L.bp_job_destroy.restype = None
+                L.bp_akima_motion.argtypes = [vp, c_int, c_int, vp, vp, vp]
+                L.bp_job_get_nodes.argtypes = [vp, vp]
+                L.bp_akima_motion_vjp.argtypes = [vp, c_int, c_int, vp, vp, vp, vp]
                 _lib = L
     return _lib
 

@@ -97,7 +97,13 @@ C4 = ScanConfig("c4-192^3x180v-320x240", 192, 1.33, 180, 200.0, 750.0, 1200.0, 3
 C4_GRADCHECK = ScanConfig("c4g-16^3x12v-32x24", 16, 4.0, 12, 200.0, 750.0, 1200.0, 32, 24, 6.4,
                           4, 40, 0.0, 6, 3.0, 2.0, 1040, 2040)
 
-CONFIGS = {"c1": C1, "c2": C2, "c3": C3, "c4": C4, "c4g": C4_GRADCHECK}
+# The paper's own motion-estimation setup (Sec. III-IV): 128^3 at 2 mm, 360
+# views over the full circle, SID 785 mm, SDD 1200 mm, 500 x 700 detector
+# (rows x columns) at 0.64 mm, motion of 10-node splines at 5 mm / 5 deg.
+PAPER = ScanConfig("paper-128^3x360v-700x500", 128, 2.0, 360, 360.0, 785.0, 1200.0, 700, 500,
+                   0.64, 30, 6, 0.01, 10, 5.0, 5.0, 1006, 2006)
+
+CONFIGS = {"c1": C1, "c2": C2, "c3": C3, "c4": C4, "c4g": C4_GRADCHECK, "paper": PAPER}
 
 
 def serving_job_config(job_id: int, n: int, views: int) -> ScanConfig:

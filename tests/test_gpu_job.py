@@ -122,3 +122,43 @@ def test_job_from_host_memory_and_reduces_loss():
     assert hist[-1] < hist[0]
     assert np.allclose(th.mean(axis=0), 0.0, atol=1e-12)  # gauge
     job.close()
+
+
+def test_job_akima_model_matches_oracle_loop():
+    """Two GD steps on the 6 N_n spline node values (Sec. II-B.1): theta from
+    the splines, forward, loss, VJP, chain rule, spline VJP, Eq. 6 on nodes,
+    gauge over nodes -- against the same loop through the oracle."""
+    cfg, P, _, proj, vw, geo = c1_inputs()
+    pj = proj.astype(np.float64)
+    nn = 6
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((nn, 6)) * np.array([0.5, 0.5, 0.5, 0.005, 0.005, 0.005])
+    x -= x.mean(axis=0)
+
+    def grad_nodes(x):
+        th = oracle.akima_motion(x, cfg.views)
+        Ph = oracle.compose(P, th)
+        vol = oracle.bp_forward(Ph, pj, cfg.vol_shape, cfg.spacing3, cfg.origin, vw,
+                                oracle.WEIGHT_FDK, cfg.sid)
+        _, dvol = oracle.sharpness(vol)
+        gP, _ = oracle.bp_vjp(Ph, pj, dvol, cfg.spacing3, cfg.origin, vw, oracle.WEIGHT_FDK,
+                              oracle.DERIV_CENTRAL, cfg.sid, want_proj=False)
+        return oracle.akima_motion_vjp(x, cfg.views, oracle.chain_motion(P, th, gP))
+
+    g0 = grad_nodes(x)
+    s0, t = 0.2 / np.abs(g0).max(), 0.97
+    xs, xo = [], x.copy()
+    for n in range(2):
+        xo = oracle.gd_step(xo, grad_nodes(xo), s0, t, n)
+        xs.append(xo)
+    job = MotionJob(cuda(proj), cuda(P), view_weight=cuda(vw), optimizer="gd", lr=s0, lr_rot=s0,
+                    decay=t, max_iters=2, theta0=cuda(x), motion_nodes=nn, **geo)
+    for want in xs:
+        job.step(1)
+        got = job.node_values()
+        for sl in (slice(0, 3), slice(3, 6)):
+            assert np.linalg.norm(got[:, sl] - want[:, sl]) <= 2e-3 * np.linalg.norm(want[:, sl])
+    th, _, it = job.motion()
+    assert it == 2
+    assert np.abs(th - oracle.akima_motion(job.node_values(), cfg.views)).max() < 1e-12
+    job.close()

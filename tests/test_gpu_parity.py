@@ -93,7 +93,9 @@ def test_c1_vjp(weight, deriv):
     # each product alone: the unfused kernels
     gm2, _, _ = gpu_vjp(delta, proj, P, th, cfg.spacing3, cfg.origin, vw, weight, deriv, cfg.sid,
                         want=(True, False, False))
-    assert np.array_equal(gm2, gm)
+    # the motion-only kernel sums even and odd voxels of a column separately
+    # (packed pairs), the fused one in sequence: same terms, other order
+    assert motion_rel(gm2, gm) <= 1e-6
     _, _, gD2 = gpu_vjp(delta, proj, P, th, cfg.spacing3, cfg.origin, vw, weight, deriv, cfg.sid,
                         want=(False, False, True))
     assert rel_l2(gD2, oD) <= VOL_TOL
