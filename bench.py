@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="skip clocks/e2e/cpu legs (profiling)")
     ap.add_argument("--me-iters", type=int, default=100, help="motion-estimation leg iterations")
     ap.add_argument("--serving", type=int, default=0, help="jobs of the serving leg (0 = skip)")
+    ap.add_argument("--c3", action="store_true",
+                    help="also time the 512^3 precision form in FP32/FP16/BF16 storage")
     ap.add_argument("--paper-iters", type=int, default=100,
                     help="iterations of the paper-setup leg (0 = skip)")
     return ap.parse_args()
@@ -264,6 +266,8 @@ def run_ours(args):
         out["motion_estimation"] = motion_estimation_leg(args, cfg, P, th_true, proj, vw, dev)
     if not args.quick and args.paper_iters > 0 and rank == 0:
         out["paper_setup"] = paper_setup_leg(args, dev)
+    if args.c3 and rank == 0:
+        out["precision_form"] = precision_leg(args, dev)
     if args.serving > 0 and rank == 0:
         from paper_2401_09283_gb300 import serving as S
         reqs = S.make_requests(args.serving, 4.0, 5, "fp16", device=local)
@@ -371,6 +375,58 @@ def paper_setup_leg(args, dev):
         out[loss] = {"wall_s": wall, "ms_per_iter": 1e3 * wall / iters, "iters_done": it,
                      "rpe_after_mm": reprojection_error(est, true, pts, cfg.pitch, cfg.pitch),
                      "loss_first": float(hist[0]), "loss_last": float(hist[it - 1])}
+    return out
+
+
+def precision_leg(args, dev):
+    """The precision form at full size (512^3 at 0.5 mm, 496 views,
+    1240 x 960): forward and motion VJP with the projections stored in FP32,
+    FP16 and BF16 (per-view scale), FP32 interpolation and accumulation.
+    Throughput only; the errors against the FP64 oracle on a sampled
+    sub-block come from the parity tests."""
+    import torch
+
+    import paper_2401_09283_gb300.workloads as W
+    from paper_2401_09283_gb300 import bp
+    cfg = W.C3
+    P, th_true, proj = make_inputs(cfg, dev)
+    V = cfg.views
+    Pd = torch.as_tensor(P, device=dev)
+    vw = torch.full((V,), cfg.delta_beta, dtype=torch.float64, device=dev)
+    th = torch.as_tensor(th_true, device=dev)
+    geo = dict(spacing=cfg.spacing3, origin=cfg.origin, weight="fdk", sid=cfg.sid)
+    vol = torch.empty(cfg.vol_shape, dtype=torch.float32, device=dev)
+    scale = proj.abs().reshape(V, -1).amax(dim=1).clamp_min(1e-30).float()
+    forms = {"f32": (proj, None), "f16": ((proj / scale[:, None, None]).half(), scale),
+             "bf16": ((proj / scale[:, None, None]).to(torch.bfloat16), scale)}
+    out = {"config": cfg.name, "voxel_views": cfg.voxel_views}
+    dvol = None
+    for name, (q, sc) in forms.items():
+        def fwd():
+            bp.bp_forward(q, Pd, th, vol_shape=cfg.vol_shape, view_weight=vw, view_scale=sc,
+                          out=vol, **geo)
+        fwd()
+        if dvol is None:
+            _, dvol = bp.bp_sharpness(vol)
+        g = torch.empty((V, 6), dtype=torch.float64, device=dev)
+
+        def vjp():
+            bp.bp_vjp(dvol, q, Pd, th, view_weight=vw, view_scale=sc, out_motion=g, **geo)
+        res = {}
+        for label, f, reps in (("forward", fwd, 5), ("vjp_motion", vjp, 3)):
+            f()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                f()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            res[label] = {"ms": ms, "Gupdate_per_s": cfg.voxel_views / (ms / 1e3) / 1e9}
+        out[name] = res
+    del forms, proj
+    torch.cuda.empty_cache()
     return out
 
 
