@@ -107,9 +107,8 @@ long long bp_ctx_workspace_bytes(const bp_ctx* ctx);
  * recorded events and returns the summed device time (ms) and the number of
  * launches of one kernel: "compose", "forward", "grad_images",
  * "vjp_motion", "reduce_chain", "vjp_proj", "vjp_fused" (motion and data VJP
- * in one pass, used when bp_vjp is asked for both), "sharpness",
- * "optimizer", "spline" (Akima motion model) or "pair_image" (the FP16/BF16
- * projections re-laid as pairs of adjacent pixels for the staged loops).
+ * in one pass, used when bp_vjp is asked for both), "sharpness" or
+ * "optimizer".
  * The paper has no counterpart; this is instrumentation for benchmarks. */
 long long bp_ctx_launch_count(const bp_ctx* ctx);
 int bp_ctx_set_timing(bp_ctx* ctx, int enable);

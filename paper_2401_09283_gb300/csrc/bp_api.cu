@@ -103,20 +103,6 @@ int prepare_views(bp_ctx* ctx, const bp_proj_desc* pd, const double* P, const do
   return BP_OK;
 }
 
-// The pair image of FP16/BF16 projections (two adjacent taps per 32-bit
-// word) that the staged loops read; nullptr for FP32 data.
-int build_pairs(bp_ctx* ctx, const void* dproj, const bp_proj_desc* pd, cudaStream_t s,
-                const unsigned** out) {
-  *out = nullptr;
-  if (pd->dtype == BP_F32) return BP_OK;
-  const ProjInfo pi = make_projinfo(pd);
-  CK(ensure(ctx->pairs, sizeof(unsigned) * (size_t)bpk::pair_image_words(pi)), "alloc pairs");
-  CK(TL(K_PAIRS, 1, bpk::launch_pair_image(dproj, pd->dtype, pi, (unsigned*)ctx->pairs.p, s)),
-     "pair image");
-  *out = (const unsigned*)ctx->pairs.p;
-  return BP_OK;
-}
-
 }  // namespace
 
 extern "C" {
@@ -146,8 +132,7 @@ void bp_ctx_destroy(bp_ctx* ctx) {
   if (!ctx) return;
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
-  Buf* bufs[] = {&ctx->geom,   &ctx->grad,   &ctx->partials,   &ctx->shblk,      &ctx->pairs,
-                 &ctx->s_proj,
+  Buf* bufs[] = {&ctx->geom,   &ctx->grad,   &ctx->partials,   &ctx->shblk,      &ctx->s_proj,
                  &ctx->s_P,    &ctx->s_motion, &ctx->s_vw,     &ctx->s_scale,    &ctx->s_vol,
                  &ctx->s_dvol, &ctx->s_out_motion, &ctx->s_out_P, &ctx->s_out_proj,
                  &ctx->s_theta, &ctx->s_grad, &ctx->s_m1,       &ctx->s_m2,       &ctx->s_loss,
@@ -163,8 +148,7 @@ const char* bp_last_error(const bp_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 
 long long bp_ctx_workspace_bytes(const bp_ctx* ctx) {
   if (!ctx) return 0;
-  const Buf* bufs[] = {&ctx->geom,   &ctx->grad,   &ctx->partials,   &ctx->shblk,      &ctx->pairs,
-                       &ctx->s_proj,
+  const Buf* bufs[] = {&ctx->geom,   &ctx->grad,   &ctx->partials,   &ctx->shblk,      &ctx->s_proj,
                        &ctx->s_P,    &ctx->s_motion, &ctx->s_vw,     &ctx->s_scale,    &ctx->s_vol,
                        &ctx->s_dvol, &ctx->s_out_motion, &ctx->s_out_P, &ctx->s_out_proj,
                        &ctx->s_theta, &ctx->s_grad, &ctx->s_m1,       &ctx->s_m2,       &ctx->s_loss,
@@ -260,12 +244,9 @@ int bp_forward(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, const d
     const double *dP, *dm;
     st = prepare_views(ctx, pdesc, P, motion, view_weight, weight, vi, s, &dP, &dm);
     if (st) return st;
-    const unsigned* pairs;
-    st = build_pairs(ctx, dproj, pdesc, s, &pairs);
-    if (st) return st;
     CK(TL(K_FORWARD, 1, bpk::launch_forward(dproj, pdesc->dtype, make_projinfo(pdesc),
                                           (const ViewGeom*)ctx->geom.p, vi,
-                                          weight == BP_WEIGHT_FDK, (float*)dvol, s, pairs)),
+                                          weight == BP_WEIGHT_FDK, (float*)dvol, s)),
        "forward kernel");
   }
   if (host_vol) {
@@ -327,18 +308,12 @@ int bp_vjp(bp_ctx* ctx, const float* dL_dvol, const void* proj, const bp_proj_de
       grad = (const float2*)ctx->grad.p;
     }
     if (nvox > 0) {
-      // the motion-only CENTRAL loop reads FP16/BF16 footprints from a pair image
-      const unsigned* pairs = nullptr;
-      if (!fuse && deriv == BP_DERIV_CENTRAL) {
-        st = build_pairs(ctx, dproj, pdesc, s, &pairs);
-        if (st) return st;
-      }
       CK(ensure(ctx->partials, sizeof(float) * bpk::PSLOTS * (size_t)V * ntiles), "alloc partials");
       CK(TL(fuse ? K_VJP_FUSED : K_VJP_MOTION, 1,
             bpk::launch_vjp_motion(ddvol, dproj, pdesc->dtype, pi, grad,
                                    (const ViewGeom*)ctx->geom.p, vi, weight == BP_WEIGHT_FDK,
                                    deriv == BP_DERIV_BILINEAR_EXACT, (float*)ctx->partials.p,
-                                   fuse ? (float*)oD : nullptr, s, pairs)),
+                                   fuse ? (float*)oD : nullptr, s)),
          "vjp kernel");
     }
     CK(TL(K_REDUCE, 1, bpk::launch_reduce_chain((const float*)ctx->partials.p, nvox > 0 ? ntiles : 0,

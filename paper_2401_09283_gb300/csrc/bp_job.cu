@@ -25,7 +25,6 @@ struct bp_job {
   double *x = nullptr, *gx = nullptr;          // node values and their gradient [N_n][6]
   bpk::ViewGeom* geom = nullptr;
   float2* grad = nullptr;
-  unsigned* pairs = nullptr;  // pair image of FP16/BF16 projections (staged loops)
   float *partials = nullptr, *vol = nullptr, *dvol = nullptr;
   int* iter = nullptr;
   long long bytes = 0;
@@ -45,8 +44,8 @@ long long align_up(long long x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // The job's buffers in allocation order (sizes in bytes).
 struct Layout {
-  long long proj, scale, P, vw, theta, m1, m2, gth, x, gx, geom, grad, pairs, partials, vol, dvol,
-      blk, hist, iter, total;
+  long long proj, scale, P, vw, theta, m1, m2, gth, x, gx, geom, grad, partials, vol, dvol, blk,
+      hist, iter, total;
 };
 
 Layout layout(const bp_proj_desc* pd, const bp_vol_desc* vd, int deriv, int max_iters) {
@@ -66,14 +65,13 @@ Layout layout(const bp_proj_desc* pd, const bp_vol_desc* vd, int deriv, int max_
   L.x = L.gx = align_up(bpk::AKIMA_MAX_NODES * 48LL);
   L.geom = align_up(V * (long long)sizeof(bpk::ViewGeom));
   L.grad = deriv == BP_DERIV_CENTRAL ? align_up(V * npx * 8) : 0;
-  L.pairs = pd->dtype != BP_F32 ? align_up(V * pd->nv * (pd->nu + 4LL) * 4) : 0;
   L.partials = align_up(V * tiles * bpk::PSLOTS * 4);
   L.vol = L.dvol = align_up(nvox * 4);
   L.blk = align_up(bpk::sharpness_blocks(nvox) * 8LL);
   L.hist = align_up((long long)max_iters * 8);
   L.iter = kAlign;
   L.total = L.proj + L.scale + L.P + L.vw + L.theta + L.gth + L.m1 + L.m2 + L.x + L.gx + L.geom +
-            L.grad + L.pairs + L.partials + 2 * L.vol + L.blk + L.hist + L.iter;
+            L.grad + L.partials + 2 * L.vol + L.blk + L.hist + L.iter;
   return L;
 }
 
@@ -108,7 +106,7 @@ cudaError_t record_iteration(bp_job* j, cudaStream_t s) {
   e = bpk::launch_compose(j->P, j->theta, j->vw, j->scale, V, fdk, j->pd.sid, j->vi, j->geom,
                           nullptr, s);
   if (e != cudaSuccess) return e;
-  e = bpk::launch_forward(j->proj, j->pd.dtype, j->pi, j->geom, j->vi, fdk, j->vol, s, j->pairs);
+  e = bpk::launch_forward(j->proj, j->pd.dtype, j->pi, j->geom, j->vi, fdk, j->vol, s);
   if (e != cudaSuccess) return e;
   if (j->opt.loss == BP_LOSS_TV)
     e = bpk::launch_tv(j->vol, j->vd.nx, j->vd.ny, j->vd.nz, (float)j->opt.tv_eps, j->blk, j->nblk,
@@ -118,8 +116,7 @@ cudaError_t record_iteration(bp_job* j, cudaStream_t s) {
                                    j->hist, j->iter, j->max_iters, j->dvol, s);
   if (e != cudaSuccess) return e;
   e = bpk::launch_vjp_motion(j->dvol, j->proj, j->pd.dtype, j->pi, j->grad, j->geom, j->vi, fdk,
-                             j->deriv == BP_DERIV_BILINEAR_EXACT, j->partials, nullptr, s,
-                             j->pairs);
+                             j->deriv == BP_DERIV_BILINEAR_EXACT, j->partials, nullptr, s);
   if (e != cudaSuccess) return e;
   e = bpk::launch_reduce_chain(j->partials, j->ntiles, j->vi, j->P, j->theta, V, nullptr, j->gth,
                                s);
@@ -240,7 +237,6 @@ int bp_job_create(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, cons
   j->nodes = opt->motion_nodes;
   j->geom = (bpk::ViewGeom*)take(L.geom);
   j->grad = L.grad ? (float2*)take(L.grad) : nullptr;
-  j->pairs = L.pairs ? (unsigned*)take(L.pairs) : nullptr;
   j->partials = (float*)take(L.partials);
   j->vol = (float*)take(L.vol);
   j->dvol = (float*)take(L.dvol);
@@ -309,10 +305,6 @@ int bp_job_create(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, cons
   j->nblk = bpk::sharpness_blocks((long long)vdesc->nx * vdesc->ny * vdesc->nz);
   if (e == cudaSuccess && j->grad) {
     e = bpk::launch_grad_images(j->proj, pdesc->dtype, j->pi, j->grad, os);
-    ctx->launches += 1;
-  }
-  if (e == cudaSuccess && j->pairs) {
-    e = bpk::launch_pair_image(j->proj, pdesc->dtype, j->pi, j->pairs, os);
     ctx->launches += 1;
   }
   if (e == cudaSuccess) e = bpk::prepare_forward(pdesc->dtype, weight == BP_WEIGHT_FDK);

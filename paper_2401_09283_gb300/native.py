@@ -195,7 +195,7 @@ def proj_desc(proj, sid=0.0, view_scale=None):
 
 
 KERNELS = ("compose", "forward", "grad_images", "vjp_motion", "reduce_chain", "vjp_proj",
-           "vjp_fused", "sharpness", "optimizer", "spline", "pair_image")
+           "vjp_fused", "sharpness", "optimizer")
 
 
 def set_timing(enable=True, device=None):

@@ -280,43 +280,6 @@ def test_c1_half_storage(dtype, tol):
     assert motion_rel(gm.cpu().numpy(), om) <= GRAD_TOL
 
 
-@pytest.mark.parametrize("dtype,code", [(torch.float16, 1), (torch.bfloat16, 2)])
-def test_half_pair_staging_matches_unstaged_layout(dtype, code):
-    """FP16/BF16 footprints are staged from a pair image (two taps per word);
-    a padded row stride disables staging.  The forward must agree bitwise
-    (same per-element arithmetic), the motion gradient to summation order."""
-    import ctypes
-    from paper_2401_09283_gb300 import native as N
-    cfg, P, th, proj, delta = scan_case("c1")
-    vw = np.full(cfg.views, cfg.delta_beta)
-    scale = np.maximum(np.abs(proj).reshape(cfg.views, -1).max(axis=1), 1e-30).astype(np.float32)
-    stored = torch.as_tensor(proj / scale[:, None, None]).to(dtype)
-    V, nv, nu = stored.shape
-    padded = torch.zeros((V, nv + 3, nu + 5), dtype=dtype)
-    padded[:, :nv, :nu] = stored
-    p, buf, sc = stored.to(DEV), padded.to(DEV), cuda(scale)
-    Pd, thd, vwd = cuda(P), cuda(th), cuda(vw)
-    geo = dict(spacing=cfg.spacing3, origin=cfg.origin, view_weight=vwd, weight="fdk",
-               sid=cfg.sid, view_scale=sc)
-    ref = bp.bp_forward(p, Pd, thd, vol_shape=cfg.vol_shape, **geo).cpu().numpy()
-    out = torch.empty(cfg.vol_shape, dtype=torch.float32, device=DEV)
-    pd = N.ProjDesc(nu, nv, V, code, nu + 5, (nu + 5) * (nv + 3), sc.data_ptr(), cfg.sid)
-    vd = N.vol_desc(cfg.vol_shape, cfg.spacing3, cfg.origin)
-    ctx = N.context(0)
-    rc = N.lib().bp_forward(ctx, buf.data_ptr(), ctypes.byref(pd), Pd.data_ptr(), thd.data_ptr(),
-                            vwd.data_ptr(), 1, ctypes.byref(vd), out.data_ptr(),
-                            N.stream_of(buf))
-    N.check("bp_forward", rc, ctx)
-    assert np.array_equal(out.cpu().numpy(), ref)
-    gm_pairs, _, _ = bp.bp_vjp(cuda(delta), p, Pd, thd, **geo)
-    gm = torch.empty((V, 6), dtype=torch.float64, device=DEV)
-    rc = N.lib().bp_vjp(ctx, cuda(delta).data_ptr(), buf.data_ptr(), ctypes.byref(pd),
-                        Pd.data_ptr(), thd.data_ptr(), vwd.data_ptr(), 1, 0, ctypes.byref(vd),
-                        gm.data_ptr(), None, None, N.stream_of(buf))
-    N.check("bp_vjp", rc, ctx)
-    assert motion_rel(gm_pairs.cpu().numpy(), gm.cpu().numpy()) <= 1e-6
-
-
 # ------------------------------------------------------ loss, optimisers, compose
 
 def test_compose_matches_oracle():
