@@ -86,16 +86,8 @@ cudaError_t launch_compose(const double* P, const double* theta, const double* v
                            const float* view_scale, int V, int fdk, double sid,
                            const VolInfo& vi, ViewGeom* geom, double* Phat, cudaStream_t s);
 
-// `pairs` (nullable): the pair image of FP16/BF16 projections (launch_pair_image);
-// when given, staged footprints are read from it (two taps per 32-bit load).
 cudaError_t launch_forward(const void* proj, int dtype, const ProjInfo& pi, const ViewGeom* geom,
-                           const VolInfo& vi, int fdk, float* vol, cudaStream_t s,
-                           const unsigned* pairs = nullptr);
-// Pair image of FP16/BF16 projections: [V][nv][nu + 4] words, word c of a
-// row = (d[c-4], d[c-3]) as raw 16-bit values, zero off the detector.
-long long pair_image_words(const ProjInfo& pi);
-cudaError_t launch_pair_image(const void* proj, int dtype, const ProjInfo& pi, unsigned* out,
-                              cudaStream_t s);
+                           const VolInfo& vi, int fdk, float* vol, cudaStream_t s);
 // Set the forward / motion-VJP kernels' shared-memory attributes on the
 // current device (done by the first launch anyway; call before capturing a
 // graph).
@@ -109,8 +101,7 @@ cudaError_t launch_grad_images(const void* proj, int dtype, const ProjInfo& pi, 
 // output zeroed by the caller) into the motion-VJP kernel.
 cudaError_t launch_vjp_motion(const float* dvol, const void* proj, int dtype, const ProjInfo& pi,
                               const float2* grad, const ViewGeom* geom, const VolInfo& vi,
-                              int fdk, int exact, float* partials, float* dproj, cudaStream_t s,
-                              const unsigned* pairs = nullptr);
+                              int fdk, int exact, float* partials, float* dproj, cudaStream_t s);
 
 cudaError_t launch_reduce_chain(const float* partials, int ntiles, const VolInfo& vi,
                                 const double* P, const double* theta, int V, double* dL_dPhat,

@@ -12,8 +12,6 @@
 // three FMAs for (u, v, w), one MUFU reciprocal, floor via a round-down add
 // of 1.5*2^23, bilinear interpolation with FP32 lerps (hardware texture
 // filtering is not used: its weights are 8-bit fixed point).
-#include <type_traits>
-
 #include "bp_internal.cuh"
 
 namespace bpk {
@@ -380,53 +378,6 @@ __device__ __forceinline__ void stage_issue(T* buf, const T* img, long long rs, 
   }
 }
 
-// Pair images (FP16/BF16 storage): word c of row r holds the raw 16-bit
-// values (d[r][c-4], d[r][c-3]) (low, high), zero off the detector, so one
-// 32-bit load returns two horizontally adjacent taps at any column.  Column
-// c = i + 4 holds pixel i, i = -4 .. nu-1 (row stride nu + 4 words): the
-// pair of pixel -1 is (0, d[0]).
-constexpr int PAIR_PAD = 4;
-
-// All threads: copy the staged rectangle of record t from a pair image; a
-// chunk of 4 pairs is wholly on or off the image (starts are multiples of 4
-// and so is nu + 4).
-__device__ __forceinline__ void stage_issue_pair(unsigned* buf, const unsigned* img,
-                                                 long long prs, int nu, int nv,
-                                                 const TileView& t) {
-  constexpr int P = STAGE_PITCH_BYTES / 4;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int lr = (lane * t.smag) >> 16, lc = lane - lr * t.scpr;
-  if (lr >= t.srpp) return;
-  const int cu = t.sx0 + lc * 4;
-  const bool uin = cu >= -PAIR_PAD && cu < nu;
-  for (int r = warp * t.srpp + lr; r < t.sh; r += (NT / 32) * t.srpp) {
-    unsigned* dst = buf + r * P + lc * 4;
-    const int row = t.sv0 + r;
-    if (uin && (unsigned)row < (unsigned)nv)
-      cp_async16(dst, img + (long long)row * prs + cu + PAIR_PAD);
-    else
-      *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void unpack_pair(unsigned w, float& lo, float& hi);
-template <>
-__device__ __forceinline__ void unpack_pair<__half>(unsigned w, float& lo, float& hi) {
-  const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
-  lo = f.x;
-  hi = f.y;
-}
-template <>
-__device__ __forceinline__ void unpack_pair<__nv_bfloat16>(unsigned w, float& lo, float& hi) {
-  lo = __uint_as_float(w << 16);
-  hi = __uint_as_float(w & 0xffff0000u);
-}
-template <>
-__device__ __forceinline__ void unpack_pair<float>(unsigned, float& lo, float& hi) {
-  lo = hi = 0.0f;  // never used: FP32 data is staged as is
-}
-
 template <typename T>
 __device__ __forceinline__ float tof(T x);
 template <>
@@ -497,12 +448,10 @@ __device__ __forceinline__ void forward_view_staged(const T* buf, const TileView
 
 // The same from the staged footprint with packed pairs of voxels (k, k+1):
 // every step of the scalar loop above, in the same order, on f32x2 pairs.
-template <int ZB, typename T, bool FDK, bool PAIR>
-__device__ __forceinline__ void forward_view_staged2(const void* vbuf, const TileView& t, float dx,
+template <int ZB, typename T, bool FDK>
+__device__ __forceinline__ void forward_view_staged2(const T* buf, const TileView& t, float dx,
                                                      float dy, f2 (&acc)[ZB / 2]) {
-  using S = typename std::conditional<PAIR, unsigned, T>::type;
-  const S* buf = static_cast<const S*>(vbuf);
-  constexpr int P = StageGeom<S>::P;
+  constexpr int P = StageGeom<T>::P;
   const float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
   const float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
   const float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
@@ -523,25 +472,10 @@ __device__ __forceinline__ void forward_view_staged2(const void* vbuf, const Til
     float bxl, bxh, byl, byh;
     up2(rx, bxl, bxh);
     up2(ry, byl, byh);
-    const S* ql = staged_tap(buf, t, __float_as_int(bxl), __float_as_int(byl));
-    const S* qh = staged_tap(buf, t, __float_as_int(bxh), __float_as_int(byh));
-    f2 d00, d10, d01, d11;
-    if constexpr (PAIR) {  // two loads per voxel: (d00, d10) and (d01, d11)
-      float a0, a1, b0, b1, c0, c1, e0, e1;
-      unpack_pair<T>(ql[0], a0, a1);
-      unpack_pair<T>(qh[0], b0, b1);
-      unpack_pair<T>(ql[P], c0, c1);
-      unpack_pair<T>(qh[P], e0, e1);
-      d00 = pk2(a0, b0);
-      d10 = pk2(a1, b1);
-      d01 = pk2(c0, e0);
-      d11 = pk2(c1, e1);
-    } else {
-      d00 = pk2(tof(ql[0]), tof(qh[0]));
-      d10 = pk2(tof(ql[1]), tof(qh[1]));
-      d01 = pk2(tof(ql[P]), tof(qh[P]));
-      d11 = pk2(tof(ql[P + 1]), tof(qh[P + 1]));
-    }
+    const T* ql = staged_tap(buf, t, __float_as_int(bxl), __float_as_int(byl));
+    const T* qh = staged_tap(buf, t, __float_as_int(bxh), __float_as_int(byh));
+    const f2 d00 = pk2(tof(ql[0]), tof(qh[0])), d10 = pk2(tof(ql[1]), tof(qh[1]));
+    const f2 d01 = pk2(tof(ql[P]), tof(qh[P])), d11 = pk2(tof(ql[P + 1]), tof(qh[P + 1]));
     const f2 val = bilerp2(tu, tv, d00, d10, d01, d11);
     acc[p] = fma2(val, FDK ? mul2(r, mul2(r, WG)) : WG, acc[p]);
   }
@@ -560,19 +494,14 @@ __device__ __forceinline__ void forward_view_staged2(const void* vbuf, const Til
 #endif
 constexpr int FWD_NBUF = BP_FWD_NBUF;
 
-//
-// With PAIR (FP16/BF16 data) the footprints are staged from the pair image
-// `pairs` instead of `proj`; unstaged tiles still read `proj`.
-template <int ZB, typename T, bool FDK, bool STAGE, bool PAIR>
+template <int ZB, typename T, bool FDK, bool STAGE>
 __global__ void __launch_bounds__(NT, FWD_MINB)
-    forward_kernel(const T* __restrict__ proj, const unsigned* __restrict__ pairs, ProjInfo pi,
-                   const ViewGeom* __restrict__ geom, VolInfo vi, float* __restrict__ vol) {
-  using S = typename std::conditional<PAIR, unsigned, T>::type;
+    forward_kernel(const T* __restrict__ proj, ProjInfo pi, const ViewGeom* __restrict__ geom,
+                   VolInfo vi, float* __restrict__ vol) {
   __shared__ TileView tvs[2][VB];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  S* bufs = reinterpret_cast<S*>(dyn_smem);
-  constexpr int CAP = STAGE_BYTES / (int)sizeof(S);
-  const long long prs = pi.nu + PAIR_PAD, pvs = (long long)pi.nv * prs;
+  T* bufs = reinterpret_cast<T*>(dyn_smem);
+  constexpr int CAP = STAGE_BYTES / (int)sizeof(T);
   static_assert(ZB % 2 == 0, "voxel pairs");
   const TileIdx ti = tile_index<ZB>(vi, blockIdx.x);
   f2 acc[ZB / 2];
@@ -580,22 +509,16 @@ __global__ void __launch_bounds__(NT, FWD_MINB)
   for (int k = 0; k < ZB / 2; ++k) acc[k] = pk2(0.0f, 0.0f);
   const int V = pi.nviews;
   const int nbatch = (V + VB - 1) / VB;
-  setup_batch<S, STAGE>(tvs[0], geom, 0, min(VB, V), ti, pi.nu, pi.nv, true);
-  if (nbatch > 1) setup_batch<S, STAGE>(tvs[1], geom, VB, min(VB, V - VB), ti, pi.nu, pi.nv, true);
+  setup_batch<T, STAGE>(tvs[0], geom, 0, min(VB, V), ti, pi.nu, pi.nv, true);
+  if (nbatch > 1) setup_batch<T, STAGE>(tvs[1], geom, VB, min(VB, V - VB), ti, pi.nu, pi.nv, true);
   __syncthreads();
-  auto issue = [&](S* buf, int view, const TileView& tv) {
-    if constexpr (PAIR)
-      stage_issue_pair(buf, pairs + (long long)view * pvs, prs, pi.nu, pi.nv, tv);
-    else
-      stage_issue(buf, proj + (long long)view * pi.vs, pi.rs, pi.nu, pi.nv, tv);
-  };
-  if (STAGE && V > 0 && tvs[0][0].staged) issue(bufs, 0, tvs[0][0]);
+  if (STAGE && V > 0 && tvs[0][0].staged) stage_issue(bufs, proj, pi.rs, pi.nu, pi.nv, tvs[0][0]);
   cp_async_commit();
   int cur = 0;  // buffer of view v
   for (int v = 0; v < V; ++v) {
     const int k = v / VB, b = v - k * VB;
     if (b == 0 && k >= 1 && k + 1 < nbatch) {
-      setup_batch<S, STAGE>(tvs[(k + 1) & 1], geom, (k + 1) * VB, min(VB, V - (k + 1) * VB), ti,
+      setup_batch<T, STAGE>(tvs[(k + 1) & 1], geom, (k + 1) * VB, min(VB, V - (k + 1) * VB), ti,
                             pi.nu, pi.nv, true);
       __syncthreads();
     }
@@ -604,14 +527,15 @@ __global__ void __launch_bounds__(NT, FWD_MINB)
     if (STAGE && v + 1 < V) {
       const int kn = (v + 1) / VB;
       const TileView& tn = tvs[kn & 1][v + 1 - kn * VB];
-      if (tn.staged) issue(bufs + nxt * CAP, v + 1, tn);
+      if (tn.staged)
+        stage_issue(bufs + nxt * CAP, proj + (long long)(v + 1) * pi.vs, pi.rs, pi.nu, pi.nv, tn);
     }
     cp_async_commit();
     cp_async_wait1();
     __syncthreads();
     if (t.mode != MODE_SKIP) {
       if (STAGE && t.staged) {
-        forward_view_staged2<ZB, T, FDK, PAIR>(bufs + cur * CAP, t, ti.dx, ti.dy, acc);
+        forward_view_staged2<ZB, T, FDK>(bufs + cur * CAP, t, ti.dx, ti.dy, acc);
       } else {
         const T* img = proj + (long long)v * pi.vs;
         float a[ZB];
@@ -673,95 +597,45 @@ static cudaError_t smem_attr_once(int bytes) {
 }
 
 template <typename T, bool FDK>
-static cudaError_t forward_dispatch(const void* proj, const unsigned* pairs, const ProjInfo& pi,
-                                    const ViewGeom* geom, const VolInfo& vi, float* vol,
-                                    cudaStream_t s) {
+static cudaError_t forward_dispatch(const void* proj, const ProjInfo& pi, const ViewGeom* geom,
+                                    const VolInfo& vi, float* vol, cudaStream_t s) {
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
   const int smem = FWD_NBUF * STAGE_BYTES;
-  const T* p = (const T*)proj;
   if (BP_FWD_STAGE && stageable<T>(proj, pi)) {
-    if (!std::is_same<T, float>::value && pairs) {
-      cudaError_t e = smem_attr_once<forward_kernel<ZB_FWD, T, FDK, true, true>>(smem);
-      if (e != cudaSuccess) return e;
-      forward_kernel<ZB_FWD, T, FDK, true, true><<<ntiles, NT, smem, s>>>(p, pairs, pi, geom, vi,
-                                                                          vol);
-    } else {
-      cudaError_t e = smem_attr_once<forward_kernel<ZB_FWD, T, FDK, true, false>>(smem);
-      if (e != cudaSuccess) return e;
-      forward_kernel<ZB_FWD, T, FDK, true, false><<<ntiles, NT, smem, s>>>(p, nullptr, pi, geom,
-                                                                           vi, vol);
-    }
+    cudaError_t e = smem_attr_once<forward_kernel<ZB_FWD, T, FDK, true>>(smem);
+    if (e != cudaSuccess) return e;
+    forward_kernel<ZB_FWD, T, FDK, true><<<ntiles, NT, smem, s>>>((const T*)proj, pi, geom, vi, vol);
   } else {
-    forward_kernel<ZB_FWD, T, FDK, false, false><<<ntiles, NT, 0, s>>>(p, nullptr, pi, geom, vi,
-                                                                       vol);
+    forward_kernel<ZB_FWD, T, FDK, false><<<ntiles, NT, 0, s>>>((const T*)proj, pi, geom, vi, vol);
   }
   return cudaGetLastError();
 }
 
-template <typename T>
-static cudaError_t prepare_forward_t(int fdk) {
-  const int smem = FWD_NBUF * STAGE_BYTES;
-  cudaError_t e = fdk ? smem_attr_once<forward_kernel<ZB_FWD, T, true, true, false>>(smem)
-                      : smem_attr_once<forward_kernel<ZB_FWD, T, false, true, false>>(smem);
-  if (e != cudaSuccess || std::is_same<T, float>::value) return e;
-  return fdk ? smem_attr_once<forward_kernel<ZB_FWD, T, true, true, true>>(smem)
-             : smem_attr_once<forward_kernel<ZB_FWD, T, false, true, true>>(smem);
-}
-
 cudaError_t prepare_forward(int dtype, int fdk) {
-  if (dtype == 0) return prepare_forward_t<float>(fdk);
-  if (dtype == 1) return prepare_forward_t<__half>(fdk);
-  return prepare_forward_t<__nv_bfloat16>(fdk);
+  const int smem = FWD_NBUF * STAGE_BYTES;
+  if (dtype == 0)
+    return fdk ? smem_attr_once<forward_kernel<ZB_FWD, float, true, true>>(smem)
+               : smem_attr_once<forward_kernel<ZB_FWD, float, false, true>>(smem);
+  if (dtype == 1)
+    return fdk ? smem_attr_once<forward_kernel<ZB_FWD, __half, true, true>>(smem)
+               : smem_attr_once<forward_kernel<ZB_FWD, __half, false, true>>(smem);
+  return fdk ? smem_attr_once<forward_kernel<ZB_FWD, __nv_bfloat16, true, true>>(smem)
+             : smem_attr_once<forward_kernel<ZB_FWD, __nv_bfloat16, false, true>>(smem);
 }
 
 cudaError_t launch_forward(const void* proj, int dtype, const ProjInfo& pi, const ViewGeom* geom,
-                           const VolInfo& vi_in, int fdk, float* vol, cudaStream_t s,
-                           const unsigned* pairs) {
+                           const VolInfo& vi_in, int fdk, float* vol, cudaStream_t s) {
   VolInfo vi = vi_in;  // the forward tiles z by ZB_FWD
   vi.zb = ZB_FWD;
   vi.tiles_z = (vi.nz + ZB_FWD - 1) / ZB_FWD;
   if (dtype == 0)
-    return fdk ? forward_dispatch<float, true>(proj, nullptr, pi, geom, vi, vol, s)
-               : forward_dispatch<float, false>(proj, nullptr, pi, geom, vi, vol, s);
+    return fdk ? forward_dispatch<float, true>(proj, pi, geom, vi, vol, s)
+               : forward_dispatch<float, false>(proj, pi, geom, vi, vol, s);
   if (dtype == 1)
-    return fdk ? forward_dispatch<__half, true>(proj, pairs, pi, geom, vi, vol, s)
-               : forward_dispatch<__half, false>(proj, pairs, pi, geom, vi, vol, s);
-  return fdk ? forward_dispatch<__nv_bfloat16, true>(proj, pairs, pi, geom, vi, vol, s)
-             : forward_dispatch<__nv_bfloat16, false>(proj, pairs, pi, geom, vi, vol, s);
-}
-
-// ------------------------------------------------------------ pair images
-
-__global__ void pair_image_kernel(const unsigned short* __restrict__ raw, ProjInfo pi,
-                                  unsigned* __restrict__ out) {
-  const long long w = pi.nu + PAIR_PAD;
-  const long long n = (long long)pi.nviews * pi.nv * w;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(e % w) - PAIR_PAD;
-    const long long rv = e / w;  // view * nv + row
-    const int r = (int)(rv % pi.nv);
-    const long long j = rv / pi.nv;
-    const unsigned short* row = raw + j * pi.vs + (long long)r * pi.rs;
-    const unsigned lo = (c >= 0 && c < pi.nu) ? row[c] : 0u;
-    const unsigned hi = (c + 1 >= 0 && c + 1 < pi.nu) ? row[c + 1] : 0u;
-    out[e] = lo | (hi << 16);
-  }
-}
-
-long long pair_image_words(const ProjInfo& pi) {
-  return (long long)pi.nviews * pi.nv * (pi.nu + PAIR_PAD);
-}
-
-cudaError_t launch_pair_image(const void* proj, int dtype, const ProjInfo& pi, unsigned* out,
-                              cudaStream_t s) {
-  if (dtype == 0) return cudaErrorInvalidValue;
-  const long long n = pair_image_words(pi);
-  if (n == 0) return cudaSuccess;
-  long long nb = (n + 255) / 256;
-  if (nb > 152 * 64) nb = 152 * 64;
-  pair_image_kernel<<<(int)nb, 256, 0, s>>>((const unsigned short*)proj, pi, out);
-  return cudaGetLastError();
+    return fdk ? forward_dispatch<__half, true>(proj, pi, geom, vi, vol, s)
+               : forward_dispatch<__half, false>(proj, pi, geom, vi, vol, s);
+  return fdk ? forward_dispatch<__nv_bfloat16, true>(proj, pi, geom, vi, vol, s)
+             : forward_dispatch<__nv_bfloat16, false>(proj, pi, geom, vi, vol, s);
 }
 
 // ------------------------------------------------------- gradient images
@@ -989,17 +863,12 @@ __device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, const
 // f32x2 pairs, with the w-component kept negated (na2 = -a2) so that no
 // negation instruction is needed.  Even and odd voxels are summed in the two
 // halves of the pair accumulators and added at the end.
-//
-// With PAIR the staged words are pairs (d[i], d[i+1]): six loads per voxel
-// instead of twelve.
-template <int ZB, typename T, bool FDK, bool EDGE, bool PROJ, bool PAIR>
-__device__ __forceinline__ void vjp_view_central2(const void* vbuf, float* pout, int nu, int nv,
+template <int ZB, typename T, bool FDK, bool EDGE, bool PROJ>
+__device__ __forceinline__ void vjp_view_central2(const T* buf, float* pout, int nu, int nv,
                                                   const TileView& t, float dx, float dy,
                                                   const float (&delta)[ZB], float (&S)[3],
                                                   float (&Z)[3]) {
-  using SE = typename std::conditional<PAIR, unsigned, T>::type;
-  const SE* buf = static_cast<const SE*>(vbuf);
-  constexpr int P = StageGeom<SE>::P;
+  constexpr int P = StageGeom<T>::P;
   const float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
   const float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
   const float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
@@ -1027,42 +896,14 @@ __device__ __forceinline__ void vjp_view_central2(const void* vbuf, float* pout,
     float bxl, bxh, byl, byh;
     up2(rx, bxl, bxh);
     up2(ry, byl, byh);
-    const SE* ql = staged_tap(buf, t, __float_as_int(bxl), __float_as_int(byl));
-    const SE* qh = staged_tap(buf, t, __float_as_int(bxh), __float_as_int(byh));
-    f2 a0, a1, b0, b1, b2, b3, c0, c1, c2, c3, e0, e1;
-    if constexpr (PAIR) {
-      // word o of both voxels -> X = (low of voxel k, low of voxel k+1), Y = highs
-#define BP_WORD2(o, X, Y)          \
-  {                                \
-    float xl, yl, xh, yh;          \
-    unpack_pair<T>(ql[o], xl, yl); \
-    unpack_pair<T>(qh[o], xh, yh); \
-    X = pk2(xl, xh);               \
-    Y = pk2(yl, yh);               \
-  }
-      BP_WORD2(-P, a0, a1);
-      BP_WORD2(-1, b0, b1);
-      BP_WORD2(1, b2, b3);
-      BP_WORD2(P - 1, c0, c1);
-      BP_WORD2(P + 1, c2, c3);
-      BP_WORD2(2 * P, e0, e1);
-#undef BP_WORD2
-    } else {
+    const T* ql = staged_tap(buf, t, __float_as_int(bxl), __float_as_int(byl));
+    const T* qh = staged_tap(buf, t, __float_as_int(bxh), __float_as_int(byh));
 #define BP_TAP2(o) pk2(tof(ql[o]), tof(qh[o]))
-      a0 = BP_TAP2(-P);
-      a1 = BP_TAP2(-P + 1);
-      b0 = BP_TAP2(-1);
-      b1 = BP_TAP2(0);
-      b2 = BP_TAP2(1);
-      b3 = BP_TAP2(2);
-      c0 = BP_TAP2(P - 1);
-      c1 = BP_TAP2(P);
-      c2 = BP_TAP2(P + 1);
-      c3 = BP_TAP2(P + 2);
-      e0 = BP_TAP2(2 * P);
-      e1 = BP_TAP2(2 * P + 1);
+    const f2 a0 = BP_TAP2(-P), a1 = BP_TAP2(-P + 1);
+    const f2 b0 = BP_TAP2(-1), b1 = BP_TAP2(0), b2 = BP_TAP2(1), b3 = BP_TAP2(2);
+    const f2 c0 = BP_TAP2(P - 1), c1 = BP_TAP2(P), c2 = BP_TAP2(P + 1), c3 = BP_TAP2(P + 2);
+    const f2 e0 = BP_TAP2(2 * P), e1 = BP_TAP2(2 * P + 1);
 #undef BP_TAP2
-    }
     // twice the central-difference gradient images at the four tap pixels
     const f2 gu = bilerp2(tu, tv, sub2(b2, b0), sub2(b3, b1), sub2(c2, c0), sub2(c3, c1));
     const f2 gv = bilerp2(tu, tv, sub2(c1, a0), sub2(c2, a1), sub2(e0, b1), sub2(e1, b2));
@@ -1109,21 +950,20 @@ __device__ __forceinline__ void vjp_view_central2(const void* vbuf, float* pout,
 
 // One view of one tile: the sample loop (from the staged footprint when it
 // was staged), then the warp reduce-scatter of the 12 sums into red[][b].
-template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ, bool PAIR>
-__device__ __forceinline__ void vjp_tile_view(const T* img, const float2* gimg, const void* vbuf,
+template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ>
+__device__ __forceinline__ void vjp_tile_view(const T* img, const float2* gimg, const T* buf,
                                               bool staged, float* pout, const ProjInfo& pi,
                                               const TileView& t, const TileIdx& ti,
                                               const float (&delta)[ZB],
                                               float (*red)[VB][12], int b) {
   float S[3] = {0.0f, 0.0f, 0.0f}, Z[3] = {0.0f, 0.0f, 0.0f};
-  const T* buf = static_cast<const T*>(vbuf);
   if (staged && !EXACT && !PROJ) {
     // CENTRAL footprints are staged only for central-safe, hence interior,
     // tiles.  (With the fused data VJP the per-voxel scatter needs the
     // samples unpacked, and the scalar loop measured faster there.)
-    vjp_view_central2<ZB, T, FDK, false, PROJ, PAIR>(vbuf, pout, pi.nu, pi.nv, t, ti.dx, ti.dy,
-                                                     delta, S, Z);
-  } else if (!PAIR && staged) {
+    vjp_view_central2<ZB, T, FDK, false, PROJ>(buf, pout, pi.nu, pi.nv, t, ti.dx, ti.dy, delta, S,
+                                               Z);
+  } else if (staged) {
     if (t.mode == MODE_INTERIOR || !PROJ)
       vjp_view<ZB, T, FDK, EXACT, false, PROJ, SRC_SMEM>(img, gimg, buf, pout, pi.rs, pi.nu,
                                                          pi.nv, t, ti.dx, ti.dy, delta, S, Z);
@@ -1178,31 +1018,18 @@ __device__ __forceinline__ void vjp_flush_batch(const TileView* tv, float (*red)
 // data and dL/dproj rows stay in L2.  Per tile the views of the chunk are
 // processed in order with the footprint of view j+1 copied to shared memory
 // while view j is computed (STAGE), like the forward.
-//
-// With PAIR (FP16/BF16 data, CENTRAL, motion only) the footprints are staged
-// from the pair image `pairs`.
-template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ, bool STAGE, bool PAIR>
+template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ, bool STAGE>
 __global__ void __launch_bounds__(NT, VJP_MINB)
-    vjp_motion_kernel(const float* __restrict__ dvol, const T* __restrict__ proj,
-                      const unsigned* __restrict__ pairs, ProjInfo pi,
+    vjp_motion_kernel(const float* __restrict__ dvol, const T* __restrict__ proj, ProjInfo pi,
                       const float2* __restrict__ grad, const ViewGeom* __restrict__ geom,
                       VolInfo vi, float* __restrict__ partials, float* __restrict__ dproj,
                       int vchunk) {
-  static_assert(!PAIR || (!EXACT && !PROJ && STAGE), "pair staging: CENTRAL motion VJP only");
-  using S = typename std::conditional<PAIR, unsigned, T>::type;
   __shared__ TileView tvs[2][VB];
   __shared__ float red[NT / 32][VB][12];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  S* bufs = reinterpret_cast<S*>(dyn_smem);
-  constexpr int CAP = STAGE_BYTES / (int)sizeof(S);
+  T* bufs = reinterpret_cast<T*>(dyn_smem);
+  constexpr int CAP = STAGE_BYTES / (int)sizeof(T);
   constexpr int HALO = EXACT ? 0 : 1;
-  const long long prs = pi.nu + PAIR_PAD, pvs = (long long)pi.nv * prs;
-  auto issue = [&](S* buf, int view, const TileView& tv) {
-    if constexpr (PAIR)
-      stage_issue_pair(buf, pairs + (long long)view * pvs, prs, pi.nu, pi.nv, tv);
-    else
-      stage_issue(buf, proj + (long long)view * pi.vs, pi.rs, pi.nu, pi.nv, tv);
-  };
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
   const int tile = blockIdx.x % ntiles;
   const int vbeg = (blockIdx.x / ntiles) * vchunk, vend = min(pi.nviews, vbeg + vchunk);
@@ -1220,12 +1047,13 @@ __global__ void __launch_bounds__(NT, VJP_MINB)
   }
   const bool any = __syncthreads_or(nz);
   const int nvw = vend - vbeg, nbatch = (nvw + VB - 1) / VB;
-  setup_batch<S, STAGE>(tvs[0], geom, vbeg, min(VB, nvw), ti, pi.nu, pi.nv, true, HALO, !EXACT);
+  setup_batch<T, STAGE>(tvs[0], geom, vbeg, min(VB, nvw), ti, pi.nu, pi.nv, true, HALO, !EXACT);
   if (nbatch > 1)
-    setup_batch<S, STAGE>(tvs[1], geom, vbeg + VB, min(VB, nvw - VB), ti, pi.nu, pi.nv, true, HALO,
+    setup_batch<T, STAGE>(tvs[1], geom, vbeg + VB, min(VB, nvw - VB), ti, pi.nu, pi.nv, true, HALO,
                           !EXACT);
   __syncthreads();
-  if (STAGE && any && tvs[0][0].staged) issue(bufs, vbeg, tvs[0][0]);
+  if (STAGE && any && tvs[0][0].staged)
+    stage_issue(bufs, proj + (long long)vbeg * pi.vs, pi.rs, pi.nu, pi.nv, tvs[0][0]);
   cp_async_commit();
   for (int v = vbeg; v < vend; ++v) {
     const int idx = v - vbeg, k = idx / VB, b = idx - k * VB;
@@ -1235,7 +1063,7 @@ __global__ void __launch_bounds__(NT, VJP_MINB)
                       partials);
       __syncthreads();
       if (k + 1 < nbatch)
-        setup_batch<S, STAGE>(tvs[(k + 1) & 1], geom, vbeg + (k + 1) * VB,
+        setup_batch<T, STAGE>(tvs[(k + 1) & 1], geom, vbeg + (k + 1) * VB,
                               min(VB, nvw - (k + 1) * VB), ti, pi.nu, pi.nv, true, HALO, !EXACT);
       __syncthreads();
     }
@@ -1243,7 +1071,9 @@ __global__ void __launch_bounds__(NT, VJP_MINB)
     if (STAGE && any && v + 1 < vend) {
       const int kn = (idx + 1) / VB;
       const TileView& tn = tvs[kn & 1][idx + 1 - kn * VB];
-      if (tn.staged) issue(bufs + ((idx + 1) & 1) * CAP, v + 1, tn);
+      if (tn.staged)
+        stage_issue(bufs + ((idx + 1) & 1) * CAP, proj + (long long)(v + 1) * pi.vs, pi.rs, pi.nu,
+                    pi.nv, tn);
     }
     cp_async_commit();
     cp_async_wait1();
@@ -1252,7 +1082,7 @@ __global__ void __launch_bounds__(NT, VJP_MINB)
       const T* img = proj + (long long)v * pi.vs;
       const float2* gimg = EXACT ? nullptr : grad + (long long)v * pi.nv * pi.nu;
       float* pout = PROJ ? dproj + (long long)v * pi.nv * pi.nu : nullptr;
-      vjp_tile_view<ZB, T, FDK, EXACT, PROJ, PAIR>(img, gimg, bufs + (idx & 1) * CAP,
+      vjp_tile_view<ZB, T, FDK, EXACT, PROJ>(img, gimg, bufs + (idx & 1) * CAP,
                                              STAGE && t.staged, pout, pi, t, ti, delta, red, b);
     }
     __syncthreads();
@@ -1274,105 +1104,82 @@ static int view_chunk(const ProjInfo& pi, long long bytes_per_px) {
   return (int)c;
 }
 
-template <typename T, bool FDK, bool EXACT, bool PROJ, bool STAGE, bool PAIR>
-static cudaError_t vjp_launch(const float* dvol, const void* proj, const unsigned* pairs,
-                              const ProjInfo& pi, const float2* grad, const ViewGeom* geom,
-                              const VolInfo& vi, float* partials, float* dproj, int vc,
-                              unsigned nblocks, cudaStream_t s) {
+template <typename T, bool FDK, bool EXACT, bool PROJ, bool STAGE>
+static cudaError_t vjp_launch(const float* dvol, const void* proj, const ProjInfo& pi,
+                              const float2* grad, const ViewGeom* geom, const VolInfo& vi,
+                              float* partials, float* dproj, int vc, unsigned nblocks,
+                              cudaStream_t s) {
   const int smem = STAGE ? 2 * STAGE_BYTES : 0;
   if (STAGE) {
-    cudaError_t e =
-        smem_attr_once<vjp_motion_kernel<ZB_VJP, T, FDK, EXACT, PROJ, STAGE, PAIR>>(smem);
+    cudaError_t e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, FDK, EXACT, PROJ, STAGE>>(smem);
     if (e != cudaSuccess) return e;
   }
-  vjp_motion_kernel<ZB_VJP, T, FDK, EXACT, PROJ, STAGE, PAIR><<<nblocks, NT, smem, s>>>(
-      dvol, (const T*)proj, pairs, pi, grad, geom, vi, partials, dproj, vc);
+  vjp_motion_kernel<ZB_VJP, T, FDK, EXACT, PROJ, STAGE><<<nblocks, NT, smem, s>>>(
+      dvol, (const T*)proj, pi, grad, geom, vi, partials, dproj, vc);
   return cudaGetLastError();
 }
 
 template <typename T, bool FDK, bool EXACT>
-static cudaError_t vjp_dispatch(const float* dvol, const void* proj, const unsigned* pairs,
-                                const ProjInfo& pi, const float2* grad, const ViewGeom* geom,
-                                const VolInfo& vi, float* partials, float* dproj, cudaStream_t s) {
+static cudaError_t vjp_dispatch(const float* dvol, const void* proj, const ProjInfo& pi,
+                                const float2* grad, const ViewGeom* geom, const VolInfo& vi,
+                                float* partials, float* dproj, cudaStream_t s) {
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
   const long long bpp = (long long)sizeof(T) + (EXACT ? 0 : 8) + (dproj ? 4 : 0);
   const int vc = view_chunk(pi, bpp);
   const unsigned nblocks = (unsigned)((long long)ntiles * ((pi.nviews + vc - 1) / vc));
   const bool stage = stageable<T>(proj, pi);
   if (dproj)
-    return stage ? vjp_launch<T, FDK, EXACT, true, true, false>(dvol, proj, nullptr, pi, grad,
-                                                                geom, vi, partials, dproj, vc,
-                                                                nblocks, s)
-                 : vjp_launch<T, FDK, EXACT, true, false, false>(dvol, proj, nullptr, pi, grad,
-                                                                 geom, vi, partials, dproj, vc,
-                                                                 nblocks, s);
-  if constexpr (!std::is_same<T, float>::value && !EXACT) {
-    if (stage && pairs)
-      return vjp_launch<T, FDK, EXACT, false, true, true>(dvol, proj, pairs, pi, grad, geom, vi,
-                                                          partials, nullptr, vc, nblocks, s);
-  }
-  return stage ? vjp_launch<T, FDK, EXACT, false, true, false>(dvol, proj, nullptr, pi, grad,
-                                                               geom, vi, partials, nullptr, vc,
-                                                               nblocks, s)
-               : vjp_launch<T, FDK, EXACT, false, false, false>(dvol, proj, nullptr, pi, grad,
-                                                                geom, vi, partials, nullptr, vc,
-                                                                nblocks, s);
+    return stage ? vjp_launch<T, FDK, EXACT, true, true>(dvol, proj, pi, grad, geom, vi, partials,
+                                                         dproj, vc, nblocks, s)
+                 : vjp_launch<T, FDK, EXACT, true, false>(dvol, proj, pi, grad, geom, vi,
+                                                          partials, dproj, vc, nblocks, s);
+  return stage ? vjp_launch<T, FDK, EXACT, false, true>(dvol, proj, pi, grad, geom, vi, partials,
+                                                        nullptr, vc, nblocks, s)
+               : vjp_launch<T, FDK, EXACT, false, false>(dvol, proj, pi, grad, geom, vi,
+                                                         partials, nullptr, vc, nblocks, s);
 }
 
 // Set the VJP kernels' shared-memory attributes on the current device
 // (call before capturing a graph).
-template <typename T, bool FDK>
-static cudaError_t prepare_vjp_t(int exact) {
-  const int smem = 2 * STAGE_BYTES;
-  if (exact)
-    return smem_attr_once<vjp_motion_kernel<ZB_VJP, T, FDK, true, false, true, false>>(smem);
-  cudaError_t e =
-      smem_attr_once<vjp_motion_kernel<ZB_VJP, T, FDK, false, false, true, false>>(smem);
-  if constexpr (!std::is_same<T, float>::value) {
-    if (e == cudaSuccess)
-      e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, FDK, false, false, true, true>>(smem);
-  }
-  return e;
-}
-
 cudaError_t prepare_vjp(int dtype, int fdk, int exact) {
-  if (dtype == 0)
-    return fdk ? prepare_vjp_t<float, true>(exact) : prepare_vjp_t<float, false>(exact);
-  if (dtype == 1)
-    return fdk ? prepare_vjp_t<__half, true>(exact) : prepare_vjp_t<__half, false>(exact);
-  return fdk ? prepare_vjp_t<__nv_bfloat16, true>(exact)
-             : prepare_vjp_t<__nv_bfloat16, false>(exact);
+  const int smem = 2 * STAGE_BYTES;
+  cudaError_t e = cudaSuccess;
+#define BP_PREP(T)                                                                                 \
+  do {                                                                                             \
+    if (fdk && exact) e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, true, true, false, true>>(smem); \
+    if (fdk && !exact) e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, true, false, false, true>>(smem); \
+    if (!fdk && exact) e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, false, true, false, true>>(smem); \
+    if (!fdk && !exact) e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, false, false, false, true>>(smem); \
+  } while (0)
+  if (dtype == 0) BP_PREP(float);
+  else if (dtype == 1) BP_PREP(__half);
+  else BP_PREP(__nv_bfloat16);
+#undef BP_PREP
+  return e;
 }
 
 template <typename T>
 static cudaError_t vjp_dispatch_t(int fdk, int exact, const float* dvol, const void* proj,
-                                  const unsigned* pairs, const ProjInfo& pi, const float2* grad,
-                                  const ViewGeom* geom, const VolInfo& vi, float* partials,
-                                  float* dproj, cudaStream_t s) {
+                                  const ProjInfo& pi, const float2* grad, const ViewGeom* geom,
+                                  const VolInfo& vi, float* partials, float* dproj,
+                                  cudaStream_t s) {
   if (fdk)
-    return exact ? vjp_dispatch<T, true, true>(dvol, proj, pairs, pi, grad, geom, vi, partials,
-                                               dproj, s)
-                 : vjp_dispatch<T, true, false>(dvol, proj, pairs, pi, grad, geom, vi, partials,
-                                                dproj, s);
-  return exact ? vjp_dispatch<T, false, true>(dvol, proj, pairs, pi, grad, geom, vi, partials,
-                                              dproj, s)
-               : vjp_dispatch<T, false, false>(dvol, proj, pairs, pi, grad, geom, vi, partials,
-                                               dproj, s);
+    return exact ? vjp_dispatch<T, true, true>(dvol, proj, pi, grad, geom, vi, partials, dproj, s)
+                 : vjp_dispatch<T, true, false>(dvol, proj, pi, grad, geom, vi, partials, dproj, s);
+  return exact ? vjp_dispatch<T, false, true>(dvol, proj, pi, grad, geom, vi, partials, dproj, s)
+               : vjp_dispatch<T, false, false>(dvol, proj, pi, grad, geom, vi, partials, dproj, s);
 }
 
 cudaError_t launch_vjp_motion(const float* dvol, const void* proj, int dtype, const ProjInfo& pi,
                               const float2* grad, const ViewGeom* geom, const VolInfo& vi,
-                              int fdk, int exact, float* partials, float* dproj, cudaStream_t s,
-                              const unsigned* pairs) {
+                              int fdk, int exact, float* partials, float* dproj, cudaStream_t s) {
   if (vi.zb != ZB_VJP) return cudaErrorInvalidValue;
   if (dtype == 0)
-    return vjp_dispatch_t<float>(fdk, exact, dvol, proj, nullptr, pi, grad, geom, vi, partials,
-                                 dproj, s);
+    return vjp_dispatch_t<float>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, dproj, s);
   if (dtype == 1)
-    return vjp_dispatch_t<__half>(fdk, exact, dvol, proj, pairs, pi, grad, geom, vi, partials,
-                                  dproj, s);
-  return vjp_dispatch_t<__nv_bfloat16>(fdk, exact, dvol, proj, pairs, pi, grad, geom, vi,
-                                       partials, dproj, s);
+    return vjp_dispatch_t<__half>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, dproj, s);
+  return vjp_dispatch_t<__nv_bfloat16>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials,
+                                       dproj, s);
 }
 
 // ------------------------------------------------- VJP w.r.t. the data
