@@ -47,6 +47,12 @@ PASS_COST = {
 }
 
 
+# DRAM bytes (read + write) per launch of each kernel on the c2 workload, from
+# one ncu capture of the current kernels (profiles/forward_vjp_c2_ncu.md);
+# reported as the roofline's "traffic" for c2 only.
+NCU_TRAFFIC_C2 = {"forward": 0.4689e9, "vjp_fused": 2.3377e9, "vjp_motion": 1.4984e9}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -234,7 +240,9 @@ def run_ours(args):
     achieved = cfg.voxel_views / ((k_ms / k_n) / 1e3)
     peak, r_fp32, r_lsu = roofline_peak(dom, sms)
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9,
-            "unit": "Gupdate/s", "frac": achieved / peak, "traffic": None,
+            "unit": "Gupdate/s", "frac": achieved / peak,
+            "traffic": NCU_TRAFFIC_C2.get(dom) if cfg.name == W.C2.name else None,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read+write)",
             "peak_basis": "min(FP32 issue %.0f, LSU %.0f) Gupdate/s at %d SMs x %.0f MHz"
                           % (r_fp32 / 1e9, r_lsu / 1e9, sms, SM_MAX_MHZ)}
     kernels = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else None, "launches": v[1],
