@@ -241,14 +241,15 @@ def main():
     ap.add_argument("--sizes", default="128,192,256,384")
     ap.add_argument("--views", default="120,248,496")
     ap.add_argument("--no-baseline", action="store_true")
+    ap.add_argument("--served-dtype", default="fp16", choices=["fp16", "fp32"])
     args = ap.parse_args()
     sizes = tuple(int(x) for x in args.sizes.split(","))
     views = tuple(int(x) for x in args.views.split(","))
     opt = OptConfig(iters=args.iters, loss=args.loss)
-    req16 = make_requests(args.jobs, args.rate, args.seed, "fp16", sizes, views)
+    req16 = make_requests(args.jobs, args.rate, args.seed, args.served_dtype, sizes, views)
     served = Server(slots=args.slots, opt=opt)
     res16 = served.run(req16)
-    out = {"served_fp16": summarize(res16, req16, served)}
+    out = {"served_" + args.served_dtype: summarize(res16, req16, served)}
     if not args.no_baseline:
         req32 = make_requests(args.jobs, args.rate, args.seed, "fp32", sizes, views)
         res32 = run_sequential(req32, opt)
