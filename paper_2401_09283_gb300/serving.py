@@ -2,9 +2,10 @@
 
 Requests arrive over time (Poisson arrivals).  A request is admitted as soon
 as a slot is free and its device memory fits the HBM budget (the job API's
-admission check); admitted jobs keep all their state on the device and each
-runs on its own stream, replaying its captured iteration graph in chunks, so
-the kernels of concurrent jobs overlap on the GPU.  A finished job is read
+admission check); admitted jobs keep all their state on the device and
+replay their captured iteration graph in chunks on priority streams (oldest
+job first, the others back-filling the SMs it leaves idle), so the kernels of
+concurrent jobs overlap on the GPU.  A finished job is read
 back and freed with the stream-ordered allocator (no device-wide
 synchronisation), and the next waiting request takes its slot.
 
@@ -122,16 +123,32 @@ def _rpe(req: Request, theta: np.ndarray, device) -> float:
 
 
 class Server:
-    """Continuous-batching server: up to `slots` jobs resident and running
-    concurrently, admission by free HBM (or an explicit budget)."""
+    """Continuous-batching server: up to `slots` jobs resident at once,
+    admission by free HBM (or an explicit budget), FIFO with back-fill.
 
-    def __init__(self, device=0, slots=4, opt: OptConfig = OptConfig(), hbm_budget=0):
+    Every resident job advances in chunks of `chunk` iterations.  Chunks go to
+    the stream of the job's rank among the resident jobs: the oldest job on
+    the highest-priority stream, the next on the next one, and so on.  The
+    block scheduler then serves the oldest job first and hands the other jobs
+    only the SMs it leaves idle (the tails of its kernels), so the head job
+    runs almost as if alone while the others fill its gaps.  When the head
+    finishes, the next job's later chunks move to the top stream (motion_step
+    orders a job's work across streams)."""
+
+    def __init__(self, device=0, slots=4, opt: OptConfig = OptConfig(), hbm_budget=0, chunk=5):
         self.device = device
         self.slots = slots
         self.opt = opt
         self.hbm_budget = hbm_budget
+        self.chunk = chunk
         self.max_resident_bytes = 0
         self.max_concurrent = 0
+
+    def _streams(self, dev):
+        # lower numbers are higher priorities: rank 0 gets the greatest
+        least, greatest = torch.cuda.Stream.priority_range()
+        return [torch.cuda.Stream(dev, priority=min(greatest + k, least))
+                for k in range(self.slots)]
 
     def run(self, requests: List[Request]) -> List[Result]:
         dev = torch.device("cuda", self.device)
@@ -141,17 +158,16 @@ class Server:
                 ctx)
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting = collections.deque()
-        active = []  # dicts: req, job, stream, event, left, admitted
+        active = []  # admission order: dicts req, job, left, events, admitted
         results = []
-        streams = [torch.cuda.Stream(dev) for _ in range(self.slots)]
-        free_streams = list(range(self.slots))
+        streams = self._streams(dev)
         t0 = time.perf_counter()
         while pending or waiting or active:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
             # admission: FIFO while a slot is free and the job fits in memory
-            while waiting and free_streams:
+            while waiting and len(active) < self.slots:
                 try:
                     job = _create(waiting[0], self.opt, self.device)
                 except RuntimeError as e:
@@ -159,30 +175,29 @@ class Server:
                         break
                     raise
                 req = waiting.popleft()
-                si = free_streams.pop()
-                active.append(dict(req=req, job=job, si=si, ev=None, left=self.opt.iters,
+                active.append(dict(req=req, job=job, left=self.opt.iters, events=[],
                                    admitted=time.perf_counter() - t0))
                 resident = sum(a["job"].nbytes for a in active)
                 self.max_resident_bytes = max(self.max_resident_bytes, resident)
                 self.max_concurrent = max(self.max_concurrent, len(active))
             progressed = False
-            for a in list(active):
-                if a["ev"] is None:
-                    # queue every iteration at once: the device never waits on
-                    # the host; other jobs' streams run alongside
-                    s = streams[a["si"]]
-                    a["job"].step(a["left"], s.cuda_stream)
+            for rank, a in enumerate(list(active)):
+                a["events"] = [ev for ev in a["events"] if not ev.query()]
+                # keep two chunks queued per job, on the stream of its rank
+                while a["left"] > 0 and len(a["events"]) < 2:
+                    s = streams[rank]
+                    n = min(self.chunk, a["left"])
+                    a["job"].step(n, s.cuda_stream)
                     ev = torch.cuda.Event()
                     ev.record(s)
-                    a["ev"] = ev
-                    a["left"] = 0
+                    a["events"].append(ev)
+                    a["left"] -= n
                     progressed = True
-                elif a["ev"].query():
+                if a["left"] == 0 and not a["events"]:
                     th, hist, _ = a["job"].motion()
                     fin = time.perf_counter() - t0
                     a["job"].close()
                     active.remove(a)
-                    free_streams.append(a["si"])
                     results.append(Result(a["req"].job_id, a["req"].arrival, a["admitted"], fin,
                                           th, hist, float("nan")))
                     progressed = True
