@@ -39,6 +39,16 @@ struct StageGeom {
   static constexpr int CH = 16 / (int)sizeof(T);                // elements per chunk
   static constexpr int P = STAGE_PITCH_BYTES / (int)sizeof(T);  // row pitch in elements
 };
+// FP16/BF16 data staged with conversion: raw rows of 16-byte chunks (8
+// pixels) at a pitch of CONV_P elements are converted into an FP32 buffer of
+// the same pitch (in floats), which the sample loops read like FP32 data.
+constexpr int CONV_P = 88;
+struct ConvGeom {
+  static constexpr int CH = 8;
+  static constexpr int P = CONV_P;
+};
+constexpr int CONV_F_BYTES = CONV_P * STAGE_ROWS * 4;  // FP32 buffer
+constexpr int CONV_R_BYTES = CONV_P * STAGE_ROWS * 2;  // raw buffer
 
 template <typename T>
 __device__ __forceinline__ float ldv(const T* p);
@@ -151,7 +161,7 @@ __device__ __forceinline__ TileIdx tile_index(const VolInfo& vi, int tile) {
 // NOT clipped to the detector (off-detector pixels are staged as zeros, so
 // the sample loop needs neither checks nor clamps), if it fits the buffer.
 // With `need_csafe` only central-safe boxes are staged.
-template <typename T, bool STAGE>
+template <typename T, bool STAGE, class G = StageGeom<T>>
 __device__ void setup_batch(TileView* tvs, const ViewGeom* __restrict__ geom, int j0, int nb,
                             const TileIdx& ti, int nu, int nv, bool with_scale, int halo = 0,
                             bool need_csafe = false) {
@@ -240,7 +250,7 @@ __device__ void setup_batch(TileView* tvs, const ViewGeom* __restrict__ geom, in
       t.fh = v1 - v0 + 1;
     }
     if (STAGE && t.mode != MODE_SKIP && (!need_csafe || t.csafe)) {
-      constexpr int CH = StageGeom<T>::CH, P = StageGeom<T>::P;
+      constexpr int CH = G::CH, P = G::P;
       const int x0 = (fl_u0 - halo) & ~(CH - 1);  // floor to a chunk boundary
       const int y0 = fl_v0 - halo;
       const int cpr = (fl_u1 + halo - x0) / CH + 1;
@@ -359,10 +369,10 @@ __device__ __forceinline__ void cp_async_wait1() {
 // one chunk per lane, no divisions).  A chunk lies wholly on or off the
 // detector (chunk starts are multiples of CH and nu is), so off-detector
 // chunks and rows are written as zeros.
-template <typename T>
+template <typename T, int P = StageGeom<T>::P>
 __device__ __forceinline__ void stage_issue(T* buf, const T* img, long long rs, int nu, int nv,
                                             const TileView& t) {
-  constexpr int CH = StageGeom<T>::CH, P = StageGeom<T>::P;
+  constexpr int CH = StageGeom<T>::CH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lr = (lane * t.smag) >> 16, lc = lane - lr * t.scpr;
   if (lr >= t.srpp) return;
@@ -376,6 +386,39 @@ __device__ __forceinline__ void stage_issue(T* buf, const T* img, long long rs, 
     else
       *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
   }
+}
+
+// All threads: convert the raw FP16/BF16 rectangle of record t (staged by
+// stage_issue<T, CONV_P>) into FP32 at the same pitch, chunk by chunk with the
+// copy's thread mapping.
+template <typename T>
+__device__ __forceinline__ void convert_stage(float* F, const T* R, const TileView& t) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lr = (lane * t.smag) >> 16, lc = lane - lr * t.scpr;
+  if (lr >= t.srpp) return;
+  for (int r = warp * t.srpp + lr; r < t.sh; r += (NT / 32) * t.srpp) {
+    const uint4 w = *reinterpret_cast<const uint4*>(R + r * CONV_P + lc * 8);
+    const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+    float f[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if constexpr (std::is_same<T, __half>::value) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&ws[q]));
+        f[2 * q] = v.x;
+        f[2 * q + 1] = v.y;
+      } else {
+        f[2 * q] = __uint_as_float(ws[q] << 16);
+        f[2 * q + 1] = __uint_as_float(ws[q] & 0xffff0000u);
+      }
+    }
+    float4* d = reinterpret_cast<float4*>(F + r * CONV_P + lc * 8);
+    d[0] = make_float4(f[0], f[1], f[2], f[3]);
+    d[1] = make_float4(f[4], f[5], f[6], f[7]);
+  }
+}
+
+__device__ __forceinline__ void cp_async_wait0() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 template <typename T>
@@ -395,9 +438,9 @@ __device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 x) {
 
 // A sample's position in the staged buffer: (bx, by) are the bit patterns
 // of x + MAGIC and y + MAGIC rounded down, i.e. MAGIC_BITS + floor.
-template <typename T>
+template <int P, typename T>
 __device__ __forceinline__ const T* staged_tap(const T* buf, const TileView& t, int bx, int by) {
-  const unsigned o = (unsigned)by * (unsigned)StageGeom<T>::P + (unsigned)bx + (unsigned)t.soff;
+  const unsigned o = (unsigned)by * (unsigned)P + (unsigned)bx + (unsigned)t.soff;
   return buf + (int)o;
 }
 
@@ -425,33 +468,13 @@ __device__ __forceinline__ void forward_view(const T* img, long long rs, int nu,
   }
 }
 
-// One view from its staged, zero-padded footprint: no checks, no clamps,
-// tap offsets are compile-time constants.
-template <int ZB, typename T, bool FDK>
-__device__ __forceinline__ void forward_view_staged(const T* buf, const TileView& t, float dx,
-                                                    float dy, float (&acc)[ZB]) {
-  constexpr int P = StageGeom<T>::P;
-  const float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
-  const float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
-  const float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
-#pragma unroll
-  for (int k = 0; k < ZB; ++k) {
-    const float dz = k - 0.5f * (ZB - 1);
-    const Sample s = locate<false>(fmaf(dz, t.ru[2], u0), fmaf(dz, t.rv[2], v0),
-                                   fmaf(dz, t.rw[2], w0), t, 0, 0);
-    const T* q = staged_tap(buf, t, s.bx, s.by);
-    const float val = bilerp(s.tu, s.tv, tof(q[0]), tof(q[1]), tof(q[P]), tof(q[P + 1]));
-    const float wv = FDK ? s.rwi * (s.rwi * t.wgt) : t.wgt;
-    acc[k] = fmaf(val, wv, acc[k]);
-  }
-}
-
-// The same from the staged footprint with packed pairs of voxels (k, k+1):
+// One view from its staged, zero-padded footprint (no checks, no clamps, tap
+// offsets are compile-time constants), with packed pairs of voxels (k, k+1):
 // every step of the scalar loop above, in the same order, on f32x2 pairs.
-template <int ZB, typename T, bool FDK>
+// E is the staged element type, P the staged row pitch.
+template <int ZB, typename T, bool FDK, int P = StageGeom<T>::P>
 __device__ __forceinline__ void forward_view_staged2(const T* buf, const TileView& t, float dx,
                                                      float dy, f2 (&acc)[ZB / 2]) {
-  constexpr int P = StageGeom<T>::P;
   const float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
   const float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
   const float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
@@ -472,8 +495,8 @@ __device__ __forceinline__ void forward_view_staged2(const T* buf, const TileVie
     float bxl, bxh, byl, byh;
     up2(rx, bxl, bxh);
     up2(ry, byl, byh);
-    const T* ql = staged_tap(buf, t, __float_as_int(bxl), __float_as_int(byl));
-    const T* qh = staged_tap(buf, t, __float_as_int(bxh), __float_as_int(byh));
+    const T* ql = staged_tap<P>(buf, t, __float_as_int(bxl), __float_as_int(byl));
+    const T* qh = staged_tap<P>(buf, t, __float_as_int(bxh), __float_as_int(byh));
     const f2 d00 = pk2(tof(ql[0]), tof(qh[0])), d10 = pk2(tof(ql[1]), tof(qh[1]));
     const f2 d01 = pk2(tof(ql[P]), tof(qh[P])), d11 = pk2(tof(ql[P + 1]), tof(qh[P + 1]));
     const f2 val = bilerp2(tu, tv, d00, d10, d01, d11);
@@ -494,13 +517,31 @@ __device__ __forceinline__ void forward_view_staged2(const T* buf, const TileVie
 #endif
 constexpr int FWD_NBUF = BP_FWD_NBUF;
 
+//
+// FP16/BF16 data (CONV) is staged through a raw buffer and converted once per
+// (tile, view) into an FP32 buffer, so the sample loop is the FP32 one
+// (no conversion per tap): wait for the raw copy of view j, barrier, convert,
+// barrier, issue the raw copy of view j+1, compute view j.
+template <typename T>
+__host__ __device__ constexpr bool conv_staging() {
+  return !std::is_same<T, float>::value;
+}
+template <typename T>
+__host__ __device__ constexpr int fwd_smem_bytes() {
+  return conv_staging<T>() ? CONV_F_BYTES + CONV_R_BYTES : FWD_NBUF * STAGE_BYTES;
+}
+
 template <int ZB, typename T, bool FDK, bool STAGE>
 __global__ void __launch_bounds__(NT, FWD_MINB)
     forward_kernel(const T* __restrict__ proj, ProjInfo pi, const ViewGeom* __restrict__ geom,
                    VolInfo vi, float* __restrict__ vol) {
+  constexpr bool CONV = STAGE && conv_staging<T>();
+  using G = typename std::conditional<CONV, ConvGeom, StageGeom<T>>::type;
   __shared__ TileView tvs[2][VB];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  T* bufs = reinterpret_cast<T*>(dyn_smem);
+  T* bufs = reinterpret_cast<T*>(dyn_smem);  // plain: FWD_NBUF buffers of T
+  float* F = reinterpret_cast<float*>(dyn_smem);  // CONV: FP32 buffer, then the raw one
+  T* R = reinterpret_cast<T*>(dyn_smem + CONV_F_BYTES);
   constexpr int CAP = STAGE_BYTES / (int)sizeof(T);
   static_assert(ZB % 2 == 0, "voxel pairs");
   const TileIdx ti = tile_index<ZB>(vi, blockIdx.x);
@@ -509,33 +550,50 @@ __global__ void __launch_bounds__(NT, FWD_MINB)
   for (int k = 0; k < ZB / 2; ++k) acc[k] = pk2(0.0f, 0.0f);
   const int V = pi.nviews;
   const int nbatch = (V + VB - 1) / VB;
-  setup_batch<T, STAGE>(tvs[0], geom, 0, min(VB, V), ti, pi.nu, pi.nv, true);
-  if (nbatch > 1) setup_batch<T, STAGE>(tvs[1], geom, VB, min(VB, V - VB), ti, pi.nu, pi.nv, true);
+  setup_batch<T, STAGE, G>(tvs[0], geom, 0, min(VB, V), ti, pi.nu, pi.nv, true);
+  if (nbatch > 1)
+    setup_batch<T, STAGE, G>(tvs[1], geom, VB, min(VB, V - VB), ti, pi.nu, pi.nv, true);
   __syncthreads();
-  if (STAGE && V > 0 && tvs[0][0].staged) stage_issue(bufs, proj, pi.rs, pi.nu, pi.nv, tvs[0][0]);
+  if (STAGE && V > 0 && tvs[0][0].staged) {
+    if constexpr (CONV)
+      stage_issue<T, CONV_P>(R, proj, pi.rs, pi.nu, pi.nv, tvs[0][0]);
+    else
+      stage_issue(bufs, proj, pi.rs, pi.nu, pi.nv, tvs[0][0]);
+  }
   cp_async_commit();
   int cur = 0;  // buffer of view v
   for (int v = 0; v < V; ++v) {
     const int k = v / VB, b = v - k * VB;
     if (b == 0 && k >= 1 && k + 1 < nbatch) {
-      setup_batch<T, STAGE>(tvs[(k + 1) & 1], geom, (k + 1) * VB, min(VB, V - (k + 1) * VB), ti,
-                            pi.nu, pi.nv, true);
+      setup_batch<T, STAGE, G>(tvs[(k + 1) & 1], geom, (k + 1) * VB, min(VB, V - (k + 1) * VB),
+                               ti, pi.nu, pi.nv, true);
       __syncthreads();
     }
     const TileView t = tvs[k & 1][b];
     const int nxt = cur == FWD_NBUF - 1 ? 0 : cur + 1;
-    if (STAGE && v + 1 < V) {
-      const int kn = (v + 1) / VB;
-      const TileView& tn = tvs[kn & 1][v + 1 - kn * VB];
-      if (tn.staged)
-        stage_issue(bufs + nxt * CAP, proj + (long long)(v + 1) * pi.vs, pi.rs, pi.nu, pi.nv, tn);
+    const int kn = (v + 1) / VB;
+    const TileView* tn = v + 1 < V ? &tvs[kn & 1][v + 1 - kn * VB] : nullptr;
+    if constexpr (CONV) {
+      cp_async_wait0();
+      __syncthreads();  // raw view v complete; every thread is done with F
+      if (t.staged) convert_stage<T>(F, R, t);
+      __syncthreads();  // F holds view v; R is free
+      if (tn && tn->staged)
+        stage_issue<T, CONV_P>(R, proj + (long long)(v + 1) * pi.vs, pi.rs, pi.nu, pi.nv, *tn);
+      cp_async_commit();
+    } else {
+      if (STAGE && tn && tn->staged)
+        stage_issue(bufs + nxt * CAP, proj + (long long)(v + 1) * pi.vs, pi.rs, pi.nu, pi.nv, *tn);
+      cp_async_commit();
+      cp_async_wait1();
+      __syncthreads();
     }
-    cp_async_commit();
-    cp_async_wait1();
-    __syncthreads();
     if (t.mode != MODE_SKIP) {
       if (STAGE && t.staged) {
-        forward_view_staged2<ZB, T, FDK>(bufs + cur * CAP, t, ti.dx, ti.dy, acc);
+        if constexpr (CONV)
+          forward_view_staged2<ZB, float, FDK, CONV_P>(F, t, ti.dx, ti.dy, acc);
+        else
+          forward_view_staged2<ZB, T, FDK>(bufs + cur * CAP, t, ti.dx, ti.dy, acc);
       } else {
         const T* img = proj + (long long)v * pi.vs;
         float a[ZB];
@@ -549,7 +607,7 @@ __global__ void __launch_bounds__(NT, FWD_MINB)
         for (int k = 0; k < ZB / 2; ++k) acc[k] = pk2(a[2 * k], a[2 * k + 1]);
       }
     }
-    if (FWD_NBUF == 2) __syncthreads();
+    if (!CONV && FWD_NBUF == 2) __syncthreads();
     cur = nxt;
   }
   const int i = ti.tx * TX + ti.lx, j = ti.ty * TY + ti.ly;
@@ -600,7 +658,7 @@ template <typename T, bool FDK>
 static cudaError_t forward_dispatch(const void* proj, const ProjInfo& pi, const ViewGeom* geom,
                                     const VolInfo& vi, float* vol, cudaStream_t s) {
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
-  const int smem = FWD_NBUF * STAGE_BYTES;
+  const int smem = fwd_smem_bytes<T>();
   if (BP_FWD_STAGE && stageable<T>(proj, pi)) {
     cudaError_t e = smem_attr_once<forward_kernel<ZB_FWD, T, FDK, true>>(smem);
     if (e != cudaSuccess) return e;
@@ -612,15 +670,15 @@ static cudaError_t forward_dispatch(const void* proj, const ProjInfo& pi, const 
 }
 
 cudaError_t prepare_forward(int dtype, int fdk) {
-  const int smem = FWD_NBUF * STAGE_BYTES;
   if (dtype == 0)
-    return fdk ? smem_attr_once<forward_kernel<ZB_FWD, float, true, true>>(smem)
-               : smem_attr_once<forward_kernel<ZB_FWD, float, false, true>>(smem);
+    return fdk ? smem_attr_once<forward_kernel<ZB_FWD, float, true, true>>(fwd_smem_bytes<float>())
+               : smem_attr_once<forward_kernel<ZB_FWD, float, false, true>>(fwd_smem_bytes<float>());
   if (dtype == 1)
-    return fdk ? smem_attr_once<forward_kernel<ZB_FWD, __half, true, true>>(smem)
-               : smem_attr_once<forward_kernel<ZB_FWD, __half, false, true>>(smem);
-  return fdk ? smem_attr_once<forward_kernel<ZB_FWD, __nv_bfloat16, true, true>>(smem)
-             : smem_attr_once<forward_kernel<ZB_FWD, __nv_bfloat16, false, true>>(smem);
+    return fdk ? smem_attr_once<forward_kernel<ZB_FWD, __half, true, true>>(fwd_smem_bytes<__half>())
+               : smem_attr_once<forward_kernel<ZB_FWD, __half, false, true>>(fwd_smem_bytes<__half>());
+  constexpr int sb = fwd_smem_bytes<__nv_bfloat16>();
+  return fdk ? smem_attr_once<forward_kernel<ZB_FWD, __nv_bfloat16, true, true>>(sb)
+             : smem_attr_once<forward_kernel<ZB_FWD, __nv_bfloat16, false, true>>(sb);
 }
 
 cudaError_t launch_forward(const void* proj, int dtype, const ProjInfo& pi, const ViewGeom* geom,
@@ -769,13 +827,14 @@ enum { SRC_GLOBAL = 0, SRC_SMEM = 1 };
 // A staged footprint is zero-padded and covers every tap, so with SRC_SMEM
 // the coordinates are never clamped (EDGE then only guards the scatter of
 // the fused data VJP).
-template <int ZB, typename T, bool FDK, bool EXACT, bool EDGE, bool PROJ, int SRC>
-__device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, const T* buf,
+template <int ZB, typename T, bool FDK, bool EXACT, bool EDGE, bool PROJ, int SRC,
+          typename E = T, int P = StageGeom<T>::P>
+__device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, const E* buf,
                                          float* pout, long long rs, int nu, int nv,
                                          const TileView& t, float dx, float dy,
                                          const float (&delta)[ZB], float (&S)[3], float (&Z)[3]) {
   constexpr bool CLAMP = EDGE && SRC == SRC_GLOBAL;
-  constexpr int P = StageGeom<T>::P;
+  
   float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
   float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
   float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
@@ -789,7 +848,7 @@ __device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, const
     if (EXACT) {
       float d00, d10, d01, d11;
       if (SRC == SRC_SMEM) {
-        const T* q = staged_tap(buf, t, s.bx, s.by);
+        const E* q = staged_tap<P>(buf, t, s.bx, s.by);
         d00 = tof(q[0]);
         d10 = tof(q[1]);
         d01 = tof(q[P]);
@@ -805,7 +864,7 @@ __device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, const
     } else if (SRC == SRC_SMEM) {
       // central-safe interior tile: 12 staged taps around (iu, iv)
       constexpr int p = P;
-      const T* q = staged_tap(buf, t, s.bx, s.by);
+      const E* q = staged_tap<P>(buf, t, s.bx, s.by);
       const float a0 = tof(q[-p]), a1 = tof(q[-p + 1]);
       const float b0 = tof(q[-1]), b1 = tof(q[0]), b2 = tof(q[1]), b3 = tof(q[2]);
       const float c0 = tof(q[p - 1]), c1 = tof(q[p]), c2 = tof(q[p + 1]), c3 = tof(q[p + 2]);
@@ -863,12 +922,12 @@ __device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, const
 // f32x2 pairs, with the w-component kept negated (na2 = -a2) so that no
 // negation instruction is needed.  Even and odd voxels are summed in the two
 // halves of the pair accumulators and added at the end.
-template <int ZB, typename T, bool FDK, bool EDGE, bool PROJ>
+template <int ZB, typename T, bool FDK, bool EDGE, bool PROJ, int P = StageGeom<T>::P>
 __device__ __forceinline__ void vjp_view_central2(const T* buf, float* pout, int nu, int nv,
                                                   const TileView& t, float dx, float dy,
                                                   const float (&delta)[ZB], float (&S)[3],
                                                   float (&Z)[3]) {
-  constexpr int P = StageGeom<T>::P;
+  
   const float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
   const float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
   const float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
@@ -896,8 +955,8 @@ __device__ __forceinline__ void vjp_view_central2(const T* buf, float* pout, int
     float bxl, bxh, byl, byh;
     up2(rx, bxl, bxh);
     up2(ry, byl, byh);
-    const T* ql = staged_tap(buf, t, __float_as_int(bxl), __float_as_int(byl));
-    const T* qh = staged_tap(buf, t, __float_as_int(bxh), __float_as_int(byh));
+    const T* ql = staged_tap<P>(buf, t, __float_as_int(bxl), __float_as_int(byl));
+    const T* qh = staged_tap<P>(buf, t, __float_as_int(bxh), __float_as_int(byh));
 #define BP_TAP2(o) pk2(tof(ql[o]), tof(qh[o]))
     const f2 a0 = BP_TAP2(-P), a1 = BP_TAP2(-P + 1);
     const f2 b0 = BP_TAP2(-1), b1 = BP_TAP2(0), b2 = BP_TAP2(1), b3 = BP_TAP2(2);
@@ -950,8 +1009,8 @@ __device__ __forceinline__ void vjp_view_central2(const T* buf, float* pout, int
 
 // One view of one tile: the sample loop (from the staged footprint when it
 // was staged), then the warp reduce-scatter of the 12 sums into red[][b].
-template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ>
-__device__ __forceinline__ void vjp_tile_view(const T* img, const float2* gimg, const T* buf,
+template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ, typename E, int P>
+__device__ __forceinline__ void vjp_tile_view(const T* img, const float2* gimg, const E* buf,
                                               bool staged, float* pout, const ProjInfo& pi,
                                               const TileView& t, const TileIdx& ti,
                                               const float (&delta)[ZB],
@@ -961,21 +1020,21 @@ __device__ __forceinline__ void vjp_tile_view(const T* img, const float2* gimg, 
     // CENTRAL footprints are staged only for central-safe, hence interior,
     // tiles.  (With the fused data VJP the per-voxel scatter needs the
     // samples unpacked, and the scalar loop measured faster there.)
-    vjp_view_central2<ZB, T, FDK, false, PROJ>(buf, pout, pi.nu, pi.nv, t, ti.dx, ti.dy, delta, S,
-                                               Z);
+    vjp_view_central2<ZB, E, FDK, false, PROJ, P>(buf, pout, pi.nu, pi.nv, t, ti.dx, ti.dy, delta,
+                                                  S, Z);
   } else if (staged) {
     if (t.mode == MODE_INTERIOR || !PROJ)
-      vjp_view<ZB, T, FDK, EXACT, false, PROJ, SRC_SMEM>(img, gimg, buf, pout, pi.rs, pi.nu,
+      vjp_view<ZB, T, FDK, EXACT, false, PROJ, SRC_SMEM, E, P>(img, gimg, buf, pout, pi.rs, pi.nu,
                                                          pi.nv, t, ti.dx, ti.dy, delta, S, Z);
     else
-      vjp_view<ZB, T, FDK, EXACT, true, PROJ, SRC_SMEM>(img, gimg, buf, pout, pi.rs, pi.nu,
+      vjp_view<ZB, T, FDK, EXACT, true, PROJ, SRC_SMEM, E, P>(img, gimg, buf, pout, pi.rs, pi.nu,
                                                         pi.nv, t, ti.dx, ti.dy, delta, S, Z);
   } else {
     if (t.mode == MODE_INTERIOR)
-      vjp_view<ZB, T, FDK, EXACT, false, PROJ, SRC_GLOBAL>(img, gimg, buf, pout, pi.rs, pi.nu,
+      vjp_view<ZB, T, FDK, EXACT, false, PROJ, SRC_GLOBAL, E, P>(img, gimg, buf, pout, pi.rs, pi.nu,
                                                            pi.nv, t, ti.dx, ti.dy, delta, S, Z);
     else
-      vjp_view<ZB, T, FDK, EXACT, true, PROJ, SRC_GLOBAL>(img, gimg, buf, pout, pi.rs, pi.nu,
+      vjp_view<ZB, T, FDK, EXACT, true, PROJ, SRC_GLOBAL, E, P>(img, gimg, buf, pout, pi.rs, pi.nu,
                                                           pi.nv, t, ti.dx, ti.dy, delta, S, Z);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1018,16 +1077,29 @@ __device__ __forceinline__ void vjp_flush_batch(const TileView* tv, float (*red)
 // data and dL/dproj rows stay in L2.  Per tile the views of the chunk are
 // processed in order with the footprint of view j+1 copied to shared memory
 // while view j is computed (STAGE), like the forward.
+//
+// FP16/BF16 data (CONV) is staged through a raw buffer and converted once per
+// (tile, view) into an FP32 buffer: convert view j, barrier, issue the raw
+// copy of view j+1, compute view j, wait for the copy, barrier.
+template <typename T>
+__host__ __device__ constexpr int vjp_smem_bytes() {
+  return conv_staging<T>() ? CONV_F_BYTES + CONV_R_BYTES : 2 * STAGE_BYTES;
+}
+
 template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ, bool STAGE>
 __global__ void __launch_bounds__(NT, VJP_MINB)
     vjp_motion_kernel(const float* __restrict__ dvol, const T* __restrict__ proj, ProjInfo pi,
                       const float2* __restrict__ grad, const ViewGeom* __restrict__ geom,
                       VolInfo vi, float* __restrict__ partials, float* __restrict__ dproj,
                       int vchunk) {
+  constexpr bool CONV = STAGE && conv_staging<T>();
+  using G = typename std::conditional<CONV, ConvGeom, StageGeom<T>>::type;
   __shared__ TileView tvs[2][VB];
   __shared__ float red[NT / 32][VB][12];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  T* bufs = reinterpret_cast<T*>(dyn_smem);
+  T* bufs = reinterpret_cast<T*>(dyn_smem);  // plain: two buffers of T
+  float* F = reinterpret_cast<float*>(dyn_smem);  // CONV: FP32 buffer, then the raw one
+  T* R = reinterpret_cast<T*>(dyn_smem + CONV_F_BYTES);
   constexpr int CAP = STAGE_BYTES / (int)sizeof(T);
   constexpr int HALO = EXACT ? 0 : 1;
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
@@ -1047,14 +1119,22 @@ __global__ void __launch_bounds__(NT, VJP_MINB)
   }
   const bool any = __syncthreads_or(nz);
   const int nvw = vend - vbeg, nbatch = (nvw + VB - 1) / VB;
-  setup_batch<T, STAGE>(tvs[0], geom, vbeg, min(VB, nvw), ti, pi.nu, pi.nv, true, HALO, !EXACT);
+  setup_batch<T, STAGE, G>(tvs[0], geom, vbeg, min(VB, nvw), ti, pi.nu, pi.nv, true, HALO, !EXACT);
   if (nbatch > 1)
-    setup_batch<T, STAGE>(tvs[1], geom, vbeg + VB, min(VB, nvw - VB), ti, pi.nu, pi.nv, true, HALO,
-                          !EXACT);
+    setup_batch<T, STAGE, G>(tvs[1], geom, vbeg + VB, min(VB, nvw - VB), ti, pi.nu, pi.nv, true,
+                             HALO, !EXACT);
   __syncthreads();
-  if (STAGE && any && tvs[0][0].staged)
-    stage_issue(bufs, proj + (long long)vbeg * pi.vs, pi.rs, pi.nu, pi.nv, tvs[0][0]);
+  if (STAGE && any && tvs[0][0].staged) {
+    if constexpr (CONV)
+      stage_issue<T, CONV_P>(R, proj + (long long)vbeg * pi.vs, pi.rs, pi.nu, pi.nv, tvs[0][0]);
+    else
+      stage_issue(bufs, proj + (long long)vbeg * pi.vs, pi.rs, pi.nu, pi.nv, tvs[0][0]);
+  }
   cp_async_commit();
+  if constexpr (CONV) {
+    cp_async_wait0();
+    __syncthreads();
+  }
   for (int v = vbeg; v < vend; ++v) {
     const int idx = v - vbeg, k = idx / VB, b = idx - k * VB;
     if (b == 0 && k >= 1) {
@@ -1063,29 +1143,41 @@ __global__ void __launch_bounds__(NT, VJP_MINB)
                       partials);
       __syncthreads();
       if (k + 1 < nbatch)
-        setup_batch<T, STAGE>(tvs[(k + 1) & 1], geom, vbeg + (k + 1) * VB,
-                              min(VB, nvw - (k + 1) * VB), ti, pi.nu, pi.nv, true, HALO, !EXACT);
+        setup_batch<T, STAGE, G>(tvs[(k + 1) & 1], geom, vbeg + (k + 1) * VB,
+                                 min(VB, nvw - (k + 1) * VB), ti, pi.nu, pi.nv, true, HALO,
+                                 !EXACT);
       __syncthreads();
     }
     const TileView t = tvs[k & 1][b];
-    if (STAGE && any && v + 1 < vend) {
-      const int kn = (idx + 1) / VB;
-      const TileView& tn = tvs[kn & 1][idx + 1 - kn * VB];
-      if (tn.staged)
+    const int kn = (idx + 1) / VB;
+    const TileView* tn = v + 1 < vend ? &tvs[kn & 1][idx + 1 - kn * VB] : nullptr;
+    if constexpr (CONV) {
+      if (any && t.staged) convert_stage<T>(F, R, t);
+      __syncthreads();  // F holds view v; R is free
+      if (any && tn && tn->staged)
+        stage_issue<T, CONV_P>(R, proj + (long long)(v + 1) * pi.vs, pi.rs, pi.nu, pi.nv, *tn);
+      cp_async_commit();
+    } else {
+      if (STAGE && any && tn && tn->staged)
         stage_issue(bufs + ((idx + 1) & 1) * CAP, proj + (long long)(v + 1) * pi.vs, pi.rs, pi.nu,
-                    pi.nv, tn);
+                    pi.nv, *tn);
+      cp_async_commit();
+      cp_async_wait1();
+      __syncthreads();
     }
-    cp_async_commit();
-    cp_async_wait1();
-    __syncthreads();
     if (any && t.mode != MODE_SKIP) {
       const T* img = proj + (long long)v * pi.vs;
       const float2* gimg = EXACT ? nullptr : grad + (long long)v * pi.nv * pi.nu;
       float* pout = PROJ ? dproj + (long long)v * pi.nv * pi.nu : nullptr;
-      vjp_tile_view<ZB, T, FDK, EXACT, PROJ>(img, gimg, bufs + (idx & 1) * CAP,
-                                             STAGE && t.staged, pout, pi, t, ti, delta, red, b);
+      if constexpr (CONV)
+        vjp_tile_view<ZB, T, FDK, EXACT, PROJ, float, CONV_P>(img, gimg, F, t.staged, pout, pi, t,
+                                                              ti, delta, red, b);
+      else
+        vjp_tile_view<ZB, T, FDK, EXACT, PROJ, T, StageGeom<T>::P>(
+            img, gimg, bufs + (idx & 1) * CAP, STAGE && t.staged, pout, pi, t, ti, delta, red, b);
     }
-    __syncthreads();
+    if constexpr (CONV) cp_async_wait0();  // the raw copy of view v+1
+    __syncthreads();  // F and the staging buffers are free; red[][b] complete
   }
   if (nvw > 0) {
     const int kl = (nvw - 1) / VB;
@@ -1109,7 +1201,7 @@ static cudaError_t vjp_launch(const float* dvol, const void* proj, const ProjInf
                               const float2* grad, const ViewGeom* geom, const VolInfo& vi,
                               float* partials, float* dproj, int vc, unsigned nblocks,
                               cudaStream_t s) {
-  const int smem = STAGE ? 2 * STAGE_BYTES : 0;
+  const int smem = STAGE ? vjp_smem_bytes<T>() : 0;
   if (STAGE) {
     cudaError_t e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, FDK, EXACT, PROJ, STAGE>>(smem);
     if (e != cudaSuccess) return e;
@@ -1142,10 +1234,10 @@ static cudaError_t vjp_dispatch(const float* dvol, const void* proj, const ProjI
 // Set the VJP kernels' shared-memory attributes on the current device
 // (call before capturing a graph).
 cudaError_t prepare_vjp(int dtype, int fdk, int exact) {
-  const int smem = 2 * STAGE_BYTES;
   cudaError_t e = cudaSuccess;
 #define BP_PREP(T)                                                                                 \
   do {                                                                                             \
+    const int smem = vjp_smem_bytes<T>();                                                          \
     if (fdk && exact) e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, true, true, false, true>>(smem); \
     if (fdk && !exact) e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, true, false, false, true>>(smem); \
     if (!fdk && exact) e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, false, true, false, true>>(smem); \
