@@ -2,7 +2,8 @@
 its analytic Jacobian (Eqs. 4-5), the rigid motion composition (Eq. 1), the
 chain rule (Eq. 2), the gradient-descent update (Eq. 6), Adam, a sharpness
 loss, total variation, the reprojection error (Sec. IV-A) and the Akima
-spline motion model (Sec. II-B.1).
+spline motion model (Sec. II-B.1) and the FDK preprocessing of the raw
+projections (cosine weight, short-scan weights, Shepp-Logan ramp).
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package; the product path
@@ -69,6 +70,11 @@ def _load():
         lib.orc_rpe.restype = ctypes.c_double
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_akima_eval.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, dp, dp]
+        lib.orc_parker.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        lib.orc_parker.restype = ctypes.c_double
+        lib.orc_fdk_filter.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, dp]
         lib.orc_akima_jacobian.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, dp, dp]
         _lib = lib
     return _lib
@@ -263,3 +269,20 @@ def akima_motion_vjp(nodes, nviews, dL_dtheta):
     x = motion_knots(nodes.shape[0], nviews)
     xe = np.arange(nviews, dtype=np.float64)
     return np.stack([akima_jacobian(nodes[:, p], xe, x).T @ g[:, p] for p in range(6)], axis=1)
+
+
+def parker(beta, gamma, arc):
+    """Short-scan redundancy weight of the ray (beta from the scan start, fan
+    angle gamma) for a scan arc `arc` (rad)."""
+    return float(_load().orc_parker(float(beta), float(gamma), float(arc)))
+
+
+def fdk_filter(raw, pitch, sid, sdd, arc):
+    """Cosine weight, short-scan (or full-scan 1/2) weight and Shepp-Logan
+    ramp of raw line integrals (V,nv,nu), by direct convolution."""
+    raw = _f64(raw)
+    V, nv, nu = raw.shape
+    out = np.zeros_like(raw)
+    _load().orc_fdk_filter(V, nu, nv, _ptr(raw), float(pitch), float(sid), float(sdd), float(arc),
+                           _ptr(out))
+    return out
