@@ -107,8 +107,8 @@ long long bp_ctx_workspace_bytes(const bp_ctx* ctx);
  * recorded events and returns the summed device time (ms) and the number of
  * launches of one kernel: "compose", "forward", "grad_images",
  * "vjp_motion", "reduce_chain", "vjp_proj", "vjp_fused" (motion and data VJP
- * in one pass, used when bp_vjp is asked for both), "sharpness" or
- * "optimizer".
+ * in one pass, used when bp_vjp is asked for both), "sharpness",
+ * "optimizer", "spline" (Akima motion model) or "fdk_filter".
  * The paper has no counterpart; this is instrumentation for benchmarks. */
 long long bp_ctx_launch_count(const bp_ctx* ctx);
 int bp_ctx_set_timing(bp_ctx* ctx, int enable);
@@ -220,6 +220,23 @@ int bp_akima_motion(bp_ctx* ctx, int n_nodes, int nviews, const double* nodes, d
                     void* stream);
 int bp_akima_motion_vjp(bp_ctx* ctx, int n_nodes, int nviews, const double* nodes,
                         const double* dL_dtheta, double* dL_dnodes, void* stream);
+
+/* FDK preprocessing of raw line integrals (the filtering of Sec. III; the
+ * redundancy weights of a short scan):
+ *   out[j][b][a] = tau * sum_k h[a-k] * w_j(k) * c(k,b) * raw[j][b][k],
+ *   c(a,b) = SDD / sqrt(SDD^2 + x_a^2 + y_b^2)   cosine weight, x_a, y_b in mm
+ *            from the principal point ((nu-1)/2, (nv-1)/2), pixel pitch `pitch`;
+ *   h[n]   = -2 / (pi^2 tau^2 (4 n^2 - 1))      Shepp-Logan ramp, tau = pitch*SID/SDD;
+ *   w_j(k) = Parker's weight of the ray (view j, column k) for a short scan
+ *            of arc `arc` (rad, views spread evenly from the scan start,
+ *            delta = (arc - pi)/2 in place of the maximum fan angle), or 1/2
+ *            for a full scan (arc >= 2 pi).
+ * A direct linear convolution along each row (zero outside the row).
+ *   raw, out  float32 [nviews][nv][nu], contiguous, host or device;
+ *   limits    nu <= 8192; a short-scan arc must exceed pi + the full fan angle.
+ * The tables are FP64 rounded to FP32; accumulation is FP32. */
+int bp_fdk_filter(bp_ctx* ctx, const float* raw, int nviews, int nv, int nu, double pitch,
+                  double sid, double sdd, double arc, float* out, void* stream);
 
 /* ------------------------------------------------------------------ jobs
  * A motion-estimation job (Sec. II-C): everything one scan needs stays on the

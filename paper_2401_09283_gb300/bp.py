@@ -139,6 +139,22 @@ def bp_akima_motion_vjp(nodes, dL_dtheta, out=None):
     return out
 
 
+def bp_fdk_filter(raw, *, pitch, sid, sdd, arc, out=None):
+    """FDK preprocessing of raw line integrals (V,nv,nu) float32: cosine weight,
+    short-scan (or full-scan 1/2) weights, Shepp-Logan ramp along rows."""
+    if raw.dtype != torch.float32:
+        raise TypeError("raw must be float32")
+    raw = raw.contiguous()
+    V, nv, nu = raw.shape
+    if out is None:
+        out = torch.empty_like(raw)
+    ctx = N.context(N.device_of(raw, out))
+    rc = N.lib().bp_fdk_filter(ctx, N.ptr(raw), V, nv, nu, float(pitch), float(sid), float(sdd),
+                               float(arc), N.ptr(out), N.stream_of(raw, out))
+    N.check("bp_fdk_filter", rc, ctx)
+    return out
+
+
 def bp_gd_step(theta, grad, s0, t, n, gauge=True):
     """Eq. 6 step n in place on theta (V,6) float64."""
     ctx = N.context(N.device_of(theta))

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbp_gb300.so")
-SOURCES = ["bp_api.cu", "bp_job.cu", "bp_geom.cu", "bp_project.cu", "bp_noalloc.cu", "bp_spline.cu"]
+SOURCES = ["bp_api.cu", "bp_job.cu", "bp_geom.cu", "bp_project.cu", "bp_noalloc.cu", "bp_spline.cu",
+           "bp_fdk.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,5 +1,6 @@
 // C-ABI of bp_gb300 (declared in include/bp_gb300.h): argument checks,
 // workspace ownership, host/device staging and kernel launches.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -132,7 +133,8 @@ void bp_ctx_destroy(bp_ctx* ctx) {
   if (!ctx) return;
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
-  Buf* bufs[] = {&ctx->geom,   &ctx->grad,   &ctx->partials,   &ctx->shblk,      &ctx->s_proj,
+  Buf* bufs[] = {&ctx->geom,   &ctx->grad,   &ctx->partials,   &ctx->shblk,      &ctx->fdk_tab,
+                 &ctx->s_proj,
                  &ctx->s_P,    &ctx->s_motion, &ctx->s_vw,     &ctx->s_scale,    &ctx->s_vol,
                  &ctx->s_dvol, &ctx->s_out_motion, &ctx->s_out_P, &ctx->s_out_proj,
                  &ctx->s_theta, &ctx->s_grad, &ctx->s_m1,       &ctx->s_m2,       &ctx->s_loss,
@@ -148,7 +150,8 @@ const char* bp_last_error(const bp_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 
 long long bp_ctx_workspace_bytes(const bp_ctx* ctx) {
   if (!ctx) return 0;
-  const Buf* bufs[] = {&ctx->geom,   &ctx->grad,   &ctx->partials,   &ctx->shblk,      &ctx->s_proj,
+  const Buf* bufs[] = {&ctx->geom,   &ctx->grad,   &ctx->partials,   &ctx->shblk,      &ctx->fdk_tab,
+                       &ctx->s_proj,
                        &ctx->s_P,    &ctx->s_motion, &ctx->s_vw,     &ctx->s_scale,    &ctx->s_vol,
                        &ctx->s_dvol, &ctx->s_out_motion, &ctx->s_out_P, &ctx->s_out_proj,
                        &ctx->s_theta, &ctx->s_grad, &ctx->s_m1,       &ctx->s_m2,       &ctx->s_loss,
@@ -540,6 +543,39 @@ int bp_akima_motion_vjp(bp_ctx* ctx, int n_nodes, int nviews, const double* node
   if (host) {
     CK(cudaMemcpyAsync(dL_dnodes, o, sizeof(double) * 6 * n_nodes, cudaMemcpyDeviceToHost, s),
        "copy dL/dnodes");
+    CK(cudaStreamSynchronize(s), "sync");
+  }
+  return BP_OK;
+}
+
+int bp_fdk_filter(bp_ctx* ctx, const float* raw, int nviews, int nv, int nu, double pitch,
+                  double sid, double sdd, double arc, float* out, void* stream) {
+  if (!ctx) return BP_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (nviews < 0 || nv < 0 || nu < 1)
+    return fail(ctx, BP_ERR_INVALID_ARG, "bp_fdk_filter: nviews, nv >= 0 and nu >= 1 needed");
+  if (nu > bpk::FDK_MAX_NU) return fail(ctx, BP_ERR_UNSUPPORTED, "bp_fdk_filter: nu > 8192");
+  if (!(pitch > 0.0) || !(sid > 0.0) || !(sdd > 0.0) || !(arc > 0.0))
+    return fail(ctx, BP_ERR_INVALID_ARG, "bp_fdk_filter: pitch, sid, sdd, arc must be > 0");
+  if (arc < 2.0 * 3.14159265358979323846 && nviews > 1 && 0.5 * (arc - 3.14159265358979323846) <=
+                                                          atan(0.5 * (nu - 1) * pitch / sdd))
+    return fail(ctx, BP_ERR_INVALID_ARG, "bp_fdk_filter: short-scan arc below pi + fan angle");
+  const size_t n = (size_t)nviews * nv * nu;
+  if (n == 0) return BP_OK;
+  if (!raw || !out) return fail(ctx, BP_ERR_INVALID_ARG, "bp_fdk_filter: NULL array");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const void* q;
+  CK(stage_in(ctx->s_proj, raw, sizeof(float) * n, s, &q), "copy raw");
+  void* o;
+  bool host;
+  CK(stage_out(ctx->s_out_proj, out, sizeof(float) * n, &o, &host), "alloc out");
+  CK(ensure(ctx->fdk_tab, sizeof(float) * bpk::fdk_table_floats(nviews, nu)), "alloc tables");
+  CK(TL(K_FDK, 2, bpk::launch_fdk_filter((const float*)q, nviews, nv, nu, pitch, sid, sdd, arc,
+                                         (float*)ctx->fdk_tab.p, (float*)o, s)),
+     "fdk filter");
+  if (host) {
+    CK(cudaMemcpyAsync(out, o, sizeof(float) * n, cudaMemcpyDeviceToHost, s), "copy out");
     CK(cudaStreamSynchronize(s), "sync");
   }
   return BP_OK;

@@ -18,12 +18,12 @@ struct Buf {
 
 enum KernelId {
   K_COMPOSE, K_FORWARD, K_GRAD, K_VJP_MOTION, K_REDUCE, K_VJP_PROJ, K_VJP_FUSED, K_SHARPNESS,
-  K_OPT, K_SPLINE, K_COUNT
+  K_OPT, K_SPLINE, K_FDK, K_COUNT
 };
 const char* const kKernelNames[K_COUNT] = {"compose",  "forward",   "grad_images",
                                            "vjp_motion", "reduce_chain", "vjp_proj",
                                            "vjp_fused",  "sharpness", "optimizer",
-                                           "spline"};
+                                           "spline",   "fdk_filter"};
 struct Pending {
   int id;
   cudaEvent_t a, b;
@@ -41,7 +41,7 @@ struct bp_ctx {
   double total_ms[bpctx::K_COUNT] = {};
   long long count[bpctx::K_COUNT] = {};
   // workspace
-  bpctx::Buf geom, grad, partials, shblk;
+  bpctx::Buf geom, grad, partials, shblk, fdk_tab;
   // staging of host arguments
   bpctx::Buf s_proj, s_P, s_motion, s_vw, s_scale, s_vol, s_dvol, s_out_motion, s_out_P, s_out_proj,
       s_theta, s_grad, s_m1, s_m2, s_loss, s_nodes, s_out_nodes;

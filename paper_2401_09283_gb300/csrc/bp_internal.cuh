@@ -145,4 +145,13 @@ cudaError_t launch_akima_eval(int n, int V, const double* nodes, double* theta, 
 cudaError_t launch_akima_vjp(int n, int V, const double* nodes, const double* g, double* dnodes,
                              cudaStream_t s);
 
+// FDK preprocessing (bp_fdk.cu): cosine and redundancy weights, Shepp-Logan
+// ramp along rows.  `tab` holds fdk_table_floats(V, nu) floats of workspace;
+// nu <= FDK_MAX_NU (shared memory of the convolution: fdk_smem_bytes(nu)).
+constexpr int FDK_MAX_NU = 8192;
+size_t fdk_table_floats(int V, int nu);
+size_t fdk_smem_bytes(int nu);
+cudaError_t launch_fdk_filter(const float* raw, int V, int nv, int nu, double pitch, double sid,
+                              double sdd, double arc, float* tab, float* out, cudaStream_t s);
+
 }  // namespace bpk

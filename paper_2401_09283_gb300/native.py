@@ -58,7 +58,8 @@ EXPORTS = ["bp_ctx_create", "bp_ctx_destroy", "bp_last_error", "bp_ctx_workspace
            "bp_compose", "bp_forward", "bp_vjp", "bp_sharpness", "bp_tv", "bp_sharpness_noalloc",
            "bp_gd_step", "bp_adam_step", "bp_job_create", "bp_job_bytes_for", "bp_job_bytes",
            "bp_ctx_set_hbm_budget", "motion_step", "bp_job_get_motion", "bp_job_volume",
-           "bp_job_destroy", "bp_akima_motion", "bp_akima_motion_vjp", "bp_job_get_nodes"]
+           "bp_job_destroy", "bp_akima_motion", "bp_akima_motion_vjp", "bp_job_get_nodes",
+           "bp_fdk_filter"]
 
 
 def lib():
@@ -114,6 +115,8 @@ def lib():
                 L.bp_job_destroy.restype = None
                 L.bp_akima_motion.argtypes = [vp, c_int, c_int, vp, vp, vp]
                 L.bp_job_get_nodes.argtypes = [vp, vp]
+                L.bp_fdk_filter.argtypes = [vp, vp, c_int, c_int, c_int, c_double, c_double,
+                                            c_double, c_double, vp, vp]
                 L.bp_akima_motion_vjp.argtypes = [vp, c_int, c_int, vp, vp, vp, vp]
                 _lib = L
     return _lib
@@ -195,7 +198,7 @@ def proj_desc(proj, sid=0.0, view_scale=None):
 
 
 KERNELS = ("compose", "forward", "grad_images", "vjp_motion", "reduce_chain", "vjp_proj",
-           "vjp_fused", "sharpness", "optimizer")
+           "vjp_fused", "sharpness", "optimizer", "spline", "fdk_filter")
 
 
 def set_timing(enable=True, device=None):
