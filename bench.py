@@ -74,6 +74,19 @@ def parse():
     return ap.parse_args()
 
 
+def job_throughput(ms_local, units_per_step, steps, ws, device):
+    """Whole-job throughput of N independent replicas (weak scaling): the
+    slowest rank's time (max over ranks, one all-reduce of a scalar) and the
+    units all ranks processed divided by it.  Returns (ms, units/s)."""
+    import torch
+    ms = float(ms_local)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t)
+    return ms, units_per_step * ws * steps / (ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -224,13 +237,9 @@ def run_ours(args):
     launches = native.launch_count(local) - launches0
     ktimes = native.kernel_times(local)
     native.set_timing(False, local)
-    if ws > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t)
-    ms_step = ms_total / args.steps
     updates_step = PASSES * cfg.voxel_views
-    value = updates_step * ws * args.steps / (ms_total / 1e3)
+    ms_total, value = job_throughput(ms_total, updates_step, args.steps, ws, dev)
+    ms_step = ms_total / args.steps
 
     # roofline of the dominant kernel
     props = torch.cuda.get_device_properties(dev)
