@@ -66,3 +66,30 @@ def test_autograd_chain_matches_oracle_spline_jacobian():
     (akima_motion(nodes, V) * w).sum().backward()
     want = oracle.akima_motion_vjp(nodes.detach().cpu().numpy(), V, w.cpu().numpy())
     assert np.max(np.abs(nodes.grad.cpu().numpy() - want)) < 1e-10
+
+
+def test_spline_model_through_backprojection_matches_oracle():
+    """nodes -> Akima theta -> backprojection -> loss, differentiated by the
+    autograd chain (spline VJP after the motion VJP), against the oracle's
+    Jacobian chain on c1."""
+    from cases import scan_case
+    from paper_2401_09283_gb300.autograd import akima_motion, backproject
+    cfg, P, _, proj, delta = scan_case("c1")
+    rng = np.random.default_rng(9)
+    x = _nodes(rng, 6) * 0.3
+    vw = np.full(cfg.views, cfg.delta_beta)
+    nodes = torch.as_tensor(x, device=DEV).requires_grad_(True)
+    theta = akima_motion(nodes, cfg.views)
+    vol = backproject(torch.as_tensor(proj, device=DEV), theta, torch.as_tensor(P, device=DEV),
+                      vol_shape=cfg.vol_shape, spacing=cfg.spacing3, origin=cfg.origin,
+                      sid=cfg.sid, view_weight=torch.as_tensor(vw, device=DEV))
+    (vol * torch.as_tensor(delta, device=DEV)).sum().backward()
+    th = oracle.akima_motion(x, cfg.views)
+    Ph = oracle.compose(P, th)
+    gP, _ = oracle.bp_vjp(Ph, proj.astype(np.float64), delta.astype(np.float64), cfg.spacing3,
+                          cfg.origin, vw, oracle.WEIGHT_FDK, oracle.DERIV_CENTRAL, cfg.sid,
+                          want_proj=False)
+    want = oracle.akima_motion_vjp(x, cfg.views, oracle.chain_motion(P, th, gP))
+    got = nodes.grad.cpu().numpy()
+    for sl in (slice(0, 3), slice(3, 6)):
+        assert np.linalg.norm(got[:, sl] - want[:, sl]) <= 1e-3 * np.linalg.norm(want[:, sl])
