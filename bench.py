@@ -543,7 +543,18 @@ def oracle_sample(cfg, P, proj_np, seconds):
 
 
 def cpu_baseline(cfg, P, proj, seconds):
-    return oracle_sample(cfg, P, proj.cpu().numpy(), seconds)
+    """The oracle on all host cores, plus a single-threaded sample beside it."""
+    import oracle
+    pj = proj.cpu().numpy()
+    out = oracle_sample(cfg, P, pj, seconds)
+    cores = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        one = oracle_sample(cfg, P, pj, max(1.0, seconds / 4))
+    finally:
+        oracle.set_num_threads(cores)
+    out["single_thread"] = {"value": one["value"], "sample": one["sample"]}
+    return out
 
 
 def run_reference(args):

@@ -69,6 +69,7 @@ def _load():
                                 ctypes.c_double]
         lib.orc_rpe.restype = ctypes.c_double
         lib.orc_num_threads.restype = ctypes.c_int
+        lib.orc_set_num_threads.argtypes = [ctypes.c_int]
         lib.orc_akima_eval.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, dp, dp]
         lib.orc_parker.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
         lib.orc_parker.restype = ctypes.c_double
@@ -98,6 +99,11 @@ def _vol(shape, spacing, origin):
 def num_threads() -> int:
     """Threads the oracle's OpenMP loops use (OMP_NUM_THREADS or all cores)."""
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on."""
+    _load().orc_set_num_threads(int(n))
 
 
 def rigid(theta):

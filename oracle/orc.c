@@ -619,3 +619,13 @@ void orc_fdk_filter(int V, int nu, int nv, const double* raw, double pitch, doub
   }
   free(h);
 }
+
+/* Threads of the OpenMP loops from now on (1 = single-threaded timing). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  extern void omp_set_num_threads(int);
+  omp_set_num_threads(n > 0 ? n : 1);
+#else
+  (void)n;
+#endif
+}
