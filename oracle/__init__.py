@@ -75,7 +75,7 @@ def _load():
         lib.orc_parker.restype = ctypes.c_double
         lib.orc_fdk_filter.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                       ctypes.c_double, dp]
+                                       ctypes.c_double, ctypes.c_int, dp]
         lib.orc_akima_jacobian.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, dp, dp]
         _lib = lib
     return _lib
@@ -283,12 +283,14 @@ def parker(beta, gamma, arc):
     return float(_load().orc_parker(float(beta), float(gamma), float(arc)))
 
 
-def fdk_filter(raw, pitch, sid, sdd, arc):
+def fdk_filter(raw, pitch, sid, sdd, arc, ext=0):
     """Cosine weight, short-scan (or full-scan 1/2) weight and Shepp-Logan
-    ramp of raw line integrals (V,nv,nu), by direct convolution."""
+    ramp of raw line integrals (V,nv,nu), by direct convolution; ext > 0
+    extends every weighted row by ext pixels per side falling linearly to 0
+    (truncation correction)."""
     raw = _f64(raw)
     V, nv, nu = raw.shape
     out = np.zeros_like(raw)
     _load().orc_fdk_filter(V, nu, nv, _ptr(raw), float(pitch), float(sid), float(sdd), float(arc),
-                           _ptr(out))
+                           int(ext), _ptr(out))
     return out

@@ -589,17 +589,22 @@ double orc_parker(double beta, double gamma, double arc) {
 }
 
 void orc_fdk_filter(int V, int nu, int nv, const double* raw, double pitch, double sid, double sdd,
-                    double arc, double* out) {
+                    double arc, int ext, double* out) {
+  /* ext > 0: truncation correction (Sec. IV-D) -- each weighted row is
+     extended by ext pixels on either side, falling linearly from its edge
+     value to 0 (the value at extension pixel m = 1..ext is edge * (1 - m/ext)),
+     filtered, and the measured nu pixels are kept. */
   const double pi = 3.14159265358979323846;
   const double tau = pitch * sid / sdd;
   const int full = arc >= 2.0 * pi - 1e-12;
   const double dbeta = full ? arc / V : (V > 1 ? arc / (V - 1) : 0.0);
-  double* h = (double*)malloc(sizeof(double) * (size_t)(2 * nu - 1)); /* h[n + nu - 1] */
-  for (int n = -(nu - 1); n <= nu - 1; ++n)
-    h[n + nu - 1] = -2.0 / (pi * pi * tau * tau * (4.0 * (double)n * n - 1.0));
+  const int n = nu + 2 * ext;                                          /* extended row */
+  double* h = (double*)malloc(sizeof(double) * (size_t)(2 * n - 1)); /* h[m + n - 1] */
+  for (int m = -(n - 1); m <= n - 1; ++m)
+    h[m + n - 1] = -2.0 / (pi * pi * tau * tau * (4.0 * (double)m * m - 1.0));
 #pragma omp parallel for schedule(static)
   for (int j = 0; j < V; ++j) {
-    double* row = (double*)malloc(sizeof(double) * (size_t)nu);
+    double* row = (double*)malloc(sizeof(double) * (size_t)n);
     const double beta = j * dbeta;
     for (int b = 0; b < nv; ++b) {
       const double y = (b - 0.5 * (nv - 1)) * pitch;
@@ -607,11 +612,15 @@ void orc_fdk_filter(int V, int nu, int nv, const double* raw, double pitch, doub
         const double x = (k - 0.5 * (nu - 1)) * pitch;
         const double c = sdd / sqrt(sdd * sdd + x * x + y * y);
         const double w = full ? 0.5 : orc_parker(beta, atan(x / sdd), arc);
-        row[k] = w * c * raw[((size_t)j * nv + b) * nu + k];
+        row[k + ext] = w * c * raw[((size_t)j * nv + b) * nu + k];
+      }
+      for (int m = 1; m <= ext; ++m) {
+        row[ext - m] = row[ext] * (1.0 - (double)m / ext);
+        row[ext + nu - 1 + m] = row[ext + nu - 1] * (1.0 - (double)m / ext);
       }
       for (int a = 0; a < nu; ++a) {
         double s = 0.0;
-        for (int k = 0; k < nu; ++k) s += h[a - k + nu - 1] * row[k];
+        for (int k = 0; k < n; ++k) s += h[(a + ext) - k + n - 1] * row[k];
         out[((size_t)j * nv + b) * nu + a] = tau * s;
       }
     }

@@ -324,9 +324,10 @@ def shepp_logan_kernel(n_half: int, tau: float) -> np.ndarray:
 
 
 def fdk_filter(raw: torch.Tensor, cfg: ScanConfig, views: Optional[Sequence[int]] = None,
-               parker: bool = True) -> torch.Tensor:
+               parker: bool = True, ext: int = 0) -> torch.Tensor:
     """Cosine weight SDD/sqrt(SDD^2+a^2+b^2), short-scan weights of the rows
-    `views` of the scan (all by default), then the Shepp-Logan ramp along u
+    `views` of the scan (all by default), optionally (ext > 0) the rows
+    extended by ext pixels per side falling linearly to 0, then the Shepp-Logan ramp along u
     on the detector scaled to the isocenter (tau = pitch*SID/SDD):
     q = tau * (h * p), a linear convolution done by a zero-padded FFT.
     raw (V,nv,nu) -> filtered, same dtype/device."""
@@ -341,17 +342,23 @@ def fdk_filter(raw: torch.Tensor, cfg: ScanConfig, views: Optional[Sequence[int]
         rows = rows if views is None else rows[np.asarray(views)]
         p = p * torch.as_tensor(rows, dtype=dt, device=dev)[:, None, :]
     tau = cfg.pitch * cfg.sid / cfg.sdd
-    L = 1 << int(math.ceil(math.log2(2 * nu)))
-    h = shepp_logan_kernel(nu - 1, tau)
+    if ext > 0:  # truncation correction: rows extended by linear fall-off to 0
+        ramp = 1.0 - torch.arange(1, ext + 1, dtype=p.dtype, device=dev) / ext
+        left = p[..., :1] * ramp.flip(0)[None, None, :]
+        right = p[..., -1:] * ramp[None, None, :]
+        p = torch.cat([left, p, right], dim=-1)
+    n = nu + 2 * ext
+    L = 1 << int(math.ceil(math.log2(2 * n)))
+    h = shepp_logan_kernel(n - 1, tau)
     hk = np.zeros(L)
-    hk[: nu] = h[nu - 1:]                 # n = 0 .. nu-1
-    hk[L - (nu - 1):] = h[: nu - 1]       # n = -(nu-1) .. -1
+    hk[: n] = h[n - 1:]                   # m = 0 .. n-1
+    hk[L - (n - 1):] = h[: n - 1]         # m = -(n-1) .. -1
     H = torch.fft.rfft(torch.as_tensor(hk, dtype=torch.float64, device=dev))
-    out = torch.empty_like(p)
+    out = torch.empty((V, nv, nu), dtype=dt, device=dev)
     for j0 in range(0, V, 16):
         blk = p[j0:j0 + 16].to(torch.float64)
         F = torch.fft.rfft(blk, n=L, dim=-1)
-        q = torch.fft.irfft(F * H, n=L, dim=-1)[..., :nu] * tau
+        q = torch.fft.irfft(F * H, n=L, dim=-1)[..., ext:ext + nu] * tau
         out[j0:j0 + 16] = q.to(dt)
     return out
 

@@ -20,6 +20,11 @@ def test_matches_fft_generator_short_and_full_scan():
         # the generator spreads short-scan views over the arc like the geometry
         got = oracle.fdk_filter(raw, small.pitch, small.sid, small.sdd, math.radians(small.arc_deg))
         assert np.max(np.abs(got - want)) <= 1e-10 * np.max(np.abs(want))
+        # with the truncation correction (rows extended by 10 % per side)
+        want = W.fdk_filter(torch.as_tensor(raw), small, ext=4).numpy()
+        got = oracle.fdk_filter(raw, small.pitch, small.sid, small.sdd,
+                                math.radians(small.arc_deg), ext=4)
+        assert np.max(np.abs(got - want)) <= 1e-10 * np.max(np.abs(want))
 
 
 def test_ramp_impulse_response_closed_form():
@@ -45,3 +50,25 @@ def test_parker_conjugate_rays_sum_to_one():
         s = oracle.parker(b, g, arc) + oracle.parker(b + math.pi - 2 * g, -g, arc)
         assert abs(s - 1.0) < 1e-12
     assert oracle.parker(0.0, 0.0, arc) == 0.0
+
+
+def test_truncation_extension_is_a_linear_fall_off():
+    """A row that is constant c after weighting (full scan, one row at the
+    principal point, tiny pitch so the cosine weight is ~1) filtered with the
+    extension equals the filter of the explicitly extended row: c on the
+    detector and c (1 - m/E) on extension pixel m."""
+    nu, E, pitch, sid, sdd = 24, 5, 1e-3, 750.0, 1200.0
+    raw = np.full((1, 1, nu), 2.0)
+    got = oracle.fdk_filter(raw, pitch, sid, sdd, 2 * math.pi, ext=E)
+    tau = pitch * sid / sdd
+    x = (np.arange(nu) - 0.5 * (nu - 1)) * pitch
+    row = 0.5 * 2.0 * sdd / np.sqrt(sdd ** 2 + x ** 2)
+    m = np.arange(1, E + 1)
+    ext = np.concatenate([row[0] * (1 - m / E)[::-1], row, row[-1] * (1 - m / E)])
+    n = np.arange(-(nu + 2 * E - 1), nu + 2 * E)
+    h = -2.0 / (math.pi ** 2 * tau ** 2 * (4.0 * n * n - 1.0))
+    full = np.convolve(ext, h)                       # index i + j
+    want = tau * full[(nu + 2 * E - 1) + E: (nu + 2 * E - 1) + E + nu]
+    assert np.max(np.abs(got[0, 0] - want)) <= 1e-10 * np.max(np.abs(want))
+    # without the extension the result differs (the edges see the cut)
+    assert np.max(np.abs(oracle.fdk_filter(raw, pitch, sid, sdd, 2 * math.pi) - got)) > 1e-3
