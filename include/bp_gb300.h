@@ -231,12 +231,17 @@ int bp_akima_motion_vjp(bp_ctx* ctx, int n_nodes, int nviews, const double* node
  *            of arc `arc` (rad, views spread evenly from the scan start,
  *            delta = (arc - pi)/2 in place of the maximum fan angle), or 1/2
  *            for a full scan (arc >= 2 pi).
- * A direct linear convolution along each row (zero outside the row).
+ * A direct linear convolution along each row.  ext > 0 is the truncation
+ * correction of Sec. IV-D: every weighted row is extended by ext pixels on
+ * either side, falling linearly from its edge value to 0 (extension pixel
+ * m = 1..ext holds edge * (1 - m/ext)), before the convolution; the paper
+ * extends by 10 % of the width.  ext = 0: zero outside the row.
  *   raw, out  float32 [nviews][nv][nu], contiguous, host or device;
- *   limits    nu <= 8192; a short-scan arc must exceed pi + the full fan angle.
+ *   limits    nu + 2 ext <= 8192; a short-scan arc must exceed pi + the full
+ *             fan angle.
  * The tables are FP64 rounded to FP32; accumulation is FP32. */
 int bp_fdk_filter(bp_ctx* ctx, const float* raw, int nviews, int nv, int nu, double pitch,
-                  double sid, double sdd, double arc, float* out, void* stream);
+                  double sid, double sdd, double arc, int ext, float* out, void* stream);
 
 /* ------------------------------------------------------------------ jobs
  * A motion-estimation job (Sec. II-C): everything one scan needs stays on the

@@ -139,9 +139,10 @@ def bp_akima_motion_vjp(nodes, dL_dtheta, out=None):
     return out
 
 
-def bp_fdk_filter(raw, *, pitch, sid, sdd, arc, out=None):
+def bp_fdk_filter(raw, *, pitch, sid, sdd, arc, ext=0, out=None):
     """FDK preprocessing of raw line integrals (V,nv,nu) float32: cosine weight,
-    short-scan (or full-scan 1/2) weights, Shepp-Logan ramp along rows."""
+    short-scan (or full-scan 1/2) weights, optional truncation extension by
+    `ext` pixels per side (linear fall-off to 0), Shepp-Logan ramp along rows."""
     if raw.dtype != torch.float32:
         raise TypeError("raw must be float32")
     raw = raw.contiguous()
@@ -150,7 +151,7 @@ def bp_fdk_filter(raw, *, pitch, sid, sdd, arc, out=None):
         out = torch.empty_like(raw)
     ctx = N.context(N.device_of(raw, out))
     rc = N.lib().bp_fdk_filter(ctx, N.ptr(raw), V, nv, nu, float(pitch), float(sid), float(sdd),
-                               float(arc), N.ptr(out), N.stream_of(raw, out))
+                               float(arc), int(ext), N.ptr(out), N.stream_of(raw, out))
     N.check("bp_fdk_filter", rc, ctx)
     return out
 

@@ -549,12 +549,14 @@ int bp_akima_motion_vjp(bp_ctx* ctx, int n_nodes, int nviews, const double* node
 }
 
 int bp_fdk_filter(bp_ctx* ctx, const float* raw, int nviews, int nv, int nu, double pitch,
-                  double sid, double sdd, double arc, float* out, void* stream) {
+                  double sid, double sdd, double arc, int ext, float* out, void* stream) {
   if (!ctx) return BP_ERR_INVALID_ARG;
   ctx->err.clear();
-  if (nviews < 0 || nv < 0 || nu < 1)
-    return fail(ctx, BP_ERR_INVALID_ARG, "bp_fdk_filter: nviews, nv >= 0 and nu >= 1 needed");
-  if (nu > bpk::FDK_MAX_NU) return fail(ctx, BP_ERR_UNSUPPORTED, "bp_fdk_filter: nu > 8192");
+  if (nviews < 0 || nv < 0 || nu < 1 || ext < 0)
+    return fail(ctx, BP_ERR_INVALID_ARG,
+                "bp_fdk_filter: nviews, nv, ext >= 0 and nu >= 1 needed");
+  if ((long long)nu + 2LL * ext > bpk::FDK_MAX_NU)
+    return fail(ctx, BP_ERR_UNSUPPORTED, "bp_fdk_filter: nu + 2 ext > 8192");
   if (!(pitch > 0.0) || !(sid > 0.0) || !(sdd > 0.0) || !(arc > 0.0))
     return fail(ctx, BP_ERR_INVALID_ARG, "bp_fdk_filter: pitch, sid, sdd, arc must be > 0");
   if (arc < 2.0 * 3.14159265358979323846 && nviews > 1 && 0.5 * (arc - 3.14159265358979323846) <=
@@ -570,9 +572,10 @@ int bp_fdk_filter(bp_ctx* ctx, const float* raw, int nviews, int nv, int nu, dou
   void* o;
   bool host;
   CK(stage_out(ctx->s_out_proj, out, sizeof(float) * n, &o, &host), "alloc out");
-  CK(ensure(ctx->fdk_tab, sizeof(float) * bpk::fdk_table_floats(nviews, nu)), "alloc tables");
-  CK(TL(K_FDK, 2, bpk::launch_fdk_filter((const float*)q, nviews, nv, nu, pitch, sid, sdd, arc,
-                                         (float*)ctx->fdk_tab.p, (float*)o, s)),
+  CK(ensure(ctx->fdk_tab, sizeof(float) * bpk::fdk_table_floats(nviews, nu, ext)),
+     "alloc tables");
+  CK(TL(K_FDK, 2, bpk::launch_fdk_filter((const float*)q, nviews, nv, nu, ext, pitch, sid, sdd,
+                                         arc, (float*)ctx->fdk_tab.p, (float*)o, s)),
      "fdk filter");
   if (host) {
     CK(cudaMemcpyAsync(out, o, sizeof(float) * n, cudaMemcpyDeviceToHost, s), "copy out");

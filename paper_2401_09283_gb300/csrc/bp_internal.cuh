@@ -145,13 +145,15 @@ cudaError_t launch_akima_eval(int n, int V, const double* nodes, double* theta, 
 cudaError_t launch_akima_vjp(int n, int V, const double* nodes, const double* g, double* dnodes,
                              cudaStream_t s);
 
-// FDK preprocessing (bp_fdk.cu): cosine and redundancy weights, Shepp-Logan
-// ramp along rows.  `tab` holds fdk_table_floats(V, nu) floats of workspace;
-// nu <= FDK_MAX_NU (shared memory of the convolution: fdk_smem_bytes(nu)).
+// FDK preprocessing (bp_fdk.cu): cosine and redundancy weights, optional
+// truncation extension by `ext` pixels per side, Shepp-Logan ramp along rows.
+// `tab` holds fdk_table_floats(V, nu, ext) floats of workspace; nu + 2 ext <=
+// FDK_MAX_NU (shared memory of the convolution: fdk_smem_bytes(nu, ext)).
 constexpr int FDK_MAX_NU = 8192;
-size_t fdk_table_floats(int V, int nu);
-size_t fdk_smem_bytes(int nu);
-cudaError_t launch_fdk_filter(const float* raw, int V, int nv, int nu, double pitch, double sid,
-                              double sdd, double arc, float* tab, float* out, cudaStream_t s);
+size_t fdk_table_floats(int V, int nu, int ext);
+size_t fdk_smem_bytes(int nu, int ext);
+cudaError_t launch_fdk_filter(const float* raw, int V, int nv, int nu, int ext, double pitch,
+                              double sid, double sdd, double arc, float* tab, float* out,
+                              cudaStream_t s);
 
 }  // namespace bpk

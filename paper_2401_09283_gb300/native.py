@@ -116,7 +116,7 @@ def lib():
                 L.bp_akima_motion.argtypes = [vp, c_int, c_int, vp, vp, vp]
                 L.bp_job_get_nodes.argtypes = [vp, vp]
                 L.bp_fdk_filter.argtypes = [vp, vp, c_int, c_int, c_int, c_double, c_double,
-                                            c_double, c_double, vp, vp]
+                                            c_double, c_double, c_int, vp, vp]
                 L.bp_akima_motion_vjp.argtypes = [vp, c_int, c_int, vp, vp, vp, vp]
                 _lib = L
     return _lib
