@@ -21,6 +21,7 @@ import argparse
 import collections
 import dataclasses
 import json
+import math
 import time
 from typing import List, Optional
 
@@ -64,8 +65,9 @@ def make_requests(n_jobs=64, rate=4.0, seed=5, dtype="fp16", sizes=(128, 192, 25
                   views=(120, 248, 496), device=0) -> List[Request]:
     """Seeded job stream: Poisson arrivals at `rate` jobs/s, volume edge and
     view count drawn uniformly, scans simulated on the device (closed-form
-    ellipsoid line integrals through the moved geometry, 1 % noise, FDK
-    filtering) and kept in pinned host memory as the client's data."""
+    ellipsoid line integrals through the moved geometry, 1 % noise) and
+    filtered by the library (bp_fdk_filter), kept in pinned host memory as
+    the client's data."""
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_jobs))
     arrivals -= arrivals[0]
@@ -81,7 +83,8 @@ def make_requests(n_jobs=64, rate=4.0, seed=5, dtype="fp16", sizes=(128, 192, 25
         raw = W.line_integrals(W.head_phantom(cfg), Pm.cpu().numpy(), cfg.nu, cfg.nv, device=dev,
                                dtype=torch.float32, views_per_chunk=32)
         raw = W.add_noise(raw, cfg.noise, cfg.phantom_seed + 100)
-        q = W.fdk_filter(raw, cfg).float()
+        q = bp.bp_fdk_filter(raw.float().contiguous(), pitch=cfg.pitch, sid=cfg.sid, sdd=cfg.sdd,
+                             arc=math.radians(cfg.arc_deg))
         if dtype == "fp16":
             scale = q.abs().reshape(v, -1).amax(dim=1).clamp_min(1e-30)
             stored = (q / scale[:, None, None]).half()
