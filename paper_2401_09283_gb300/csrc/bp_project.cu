@@ -1185,12 +1185,15 @@ __global__ void __launch_bounds__(NT, VJP_MINB)
   }
 }
 
+#ifndef BP_VJP_CHUNK_MIB
+#define BP_VJP_CHUNK_MIB 64
+#endif
 // Views per chunk of the view-chunked VJP grids: keep the bytes that one
 // chunk's views touch (projections, gradient images, dL/dproj rows) near
 // 64 MiB, well inside the 126 MiB L2.
 static int view_chunk(const ProjInfo& pi, long long bytes_per_px) {
   const long long per_view = (long long)pi.nu * pi.nv * bytes_per_px;
-  long long c = (64LL << 20) / (per_view > 0 ? per_view : 1);
+  long long c = ((long long)BP_VJP_CHUNK_MIB << 20) / (per_view > 0 ? per_view : 1);
   if (c < 1) c = 1;
   if (c > VB) c = VB;
   return (int)c;
