@@ -50,7 +50,7 @@ PASS_COST = {
 # DRAM bytes (read + write) per launch of each kernel on the c2 workload, from
 # one ncu capture of the current kernels (profiles/forward_vjp_c2_ncu.md);
 # reported as the roofline's "traffic" for c2 only.
-NCU_TRAFFIC_C2 = {"forward": 0.4689e9, "vjp_fused": 2.3377e9, "vjp_motion": 1.4984e9}
+NCU_TRAFFIC_C2 = {"forward": 0.4700e9, "vjp_fused": 1.7366e9, "vjp_motion": 1.1013e9}
 
 
 def parse():
