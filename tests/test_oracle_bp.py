@@ -1,7 +1,7 @@
 """Pins of the oracle's backprojection (Eq. 3) and its derivatives (Eqs. 4-5):
 hand-computed cases, closed forms, the adjoint identity, affine images where
 Eq. 4 is exact, brute-force finite differences on 16^3 and the common-mode
-translation identity."""
+translation and rotation identities."""
 import math
 
 import numpy as np
@@ -219,6 +219,40 @@ def test_common_mode_translation_identity():
         rhs = np.sum(delta * (Ip - Im)) / (2 * eps)
         lhs = gth[:, ax].sum()
         assert abs(lhs - rhs) <= 2e-3 * abs(rhs) + 1e-9, (ax, lhs, rhs)
+
+
+def test_common_mode_rotation_identity():
+    """Rotating every view by the same small angle about world axis a samples
+    the zero-motion reconstruction at R_a p, so sum_j dL/dr_{a,j} =
+    sum_p delta(p) (e_a x p) . grad I0(p); grad I0 by FD of reconstructions on
+    grids shifted by +-eps (no motion involved)."""
+    cfg, P, _, proj, delta = _rand_case(6, motion=False)
+    vv, uu = np.meshgrid(np.arange(cfg.nv), np.arange(cfg.nu), indexing="ij")
+    proj = np.stack([np.cos(0.21 * uu - 0.07 * j) * np.sin(0.27 * vv + 0.3) for j in range(cfg.views)])
+    th0 = np.zeros((cfg.views, 6))
+    gP, _ = oracle.bp_vjp(P, proj, delta, cfg.spacing3, cfg.origin,
+                          deriv_mode=oracle.DERIV_BILINEAR_EXACT, want_proj=False)
+    gth = oracle.chain_motion(P, th0, gP)
+    eps = 1e-4
+    grad = []
+    for ax in range(3):
+        op, om = list(cfg.origin), list(cfg.origin)
+        op[ax] += eps
+        om[ax] -= eps
+        Ip = oracle.bp_forward(P, proj, cfg.vol_shape, cfg.spacing3, op)
+        Im = oracle.bp_forward(P, proj, cfg.vol_shape, cfg.spacing3, om)
+        grad.append((Ip - Im) / (2 * eps))          # d I0 / d x_ax, volume [z][y][x]
+    n = cfg.vol_shape[0]
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    px, py, pz = (cfg.origin[0] + i * cfg.spacing, cfg.origin[1] + j * cfg.spacing,
+                  cfg.origin[2] + k * cfg.spacing)
+    gx, gy, gz = grad
+    cross = {0: (0 * px, -pz, py), 1: (pz, 0 * px, -px), 2: (-py, px, 0 * px)}  # e_a x p
+    for a in range(3):
+        cx, cy, cz = cross[a]
+        rhs = np.sum(delta * (cx * gx + cy * gy + cz * gz))
+        lhs = gth[:, 3 + a].sum()
+        assert abs(lhs - rhs) <= 2e-3 * abs(rhs) + 1e-9, (a, lhs, rhs)
 
 
 def test_gradient_images_edges_and_interior():
