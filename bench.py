@@ -47,9 +47,11 @@ PASS_COST = {
 }
 
 
-# DRAM bytes (read + write) per launch of each kernel on the c2 workload, from
-# one ncu capture of the current kernels (profiles/forward_vjp_c2_ncu.md);
-# reported as the roofline's "traffic" for c2 only.
+# DRAM bytes (read + write) per launch of each kernel on the c2 workload:
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
+# current kernels at full c2 size (one launch each; the capture and its
+# command are kept with the profiles).  Reported as the roofline's "traffic"
+# for c2 only; it must be re-captured whenever one of these kernels changes.
 NCU_TRAFFIC_C2 = {"forward": 0.4700e9, "vjp_fused": 1.7366e9, "vjp_motion": 1.1013e9}
 
 
@@ -66,9 +68,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--quick", action="store_true", help="skip clocks/e2e/cpu legs (profiling)")
     ap.add_argument("--me-iters", type=int, default=100, help="motion-estimation leg iterations")
-    ap.add_argument("--serving", type=int, default=0, help="jobs of the serving leg (0 = skip)")
-    ap.add_argument("--c3", action="store_true",
-                    help="also time the 512^3 precision form in FP32/FP16/BF16 storage")
+    ap.add_argument("--serving", type=int, default=16, help="jobs of the serving leg (0 = skip)")
+    ap.add_argument("--serving-repeats", type=int, default=3,
+                    help="runs of each serving form (spread of jobs/s)")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="skip the 512^3 precision form (FP32/FP16/BF16 storage)")
     ap.add_argument("--paper-iters", type=int, default=100,
                     help="iterations of the paper-setup leg (0 = skip)")
     return ap.parse_args()
@@ -283,9 +287,9 @@ def run_ours(args):
         out["motion_estimation"] = motion_estimation_leg(args, cfg, P, th_true, proj, vw, dev)
     if not args.quick and args.paper_iters > 0 and rank == 0:
         out["paper_setup"] = paper_setup_leg(args, dev)
-    if args.c3 and rank == 0:
+    if not args.quick and not args.no_c3 and rank == 0:
         out["precision_form"] = precision_leg(args, dev)
-    if args.serving > 0 and rank == 0:
+    if not args.quick and args.serving > 0 and rank == 0:
         from paper_2401_09283_gb300 import serving as S
         reqs = S.make_requests(args.serving, 4.0, 5, "fp16", device=local)
         srv = S.Server(device=local, slots=4)
@@ -457,7 +461,9 @@ def precision_leg(args, dev):
 def e2e_leg(args, cfg, P, proj, vw, geo, dev):
     """Same step through the C-ABI with host buffers: projections, matrices,
     motion and optimiser state in pinned host memory, copied in by the
-    library every call; results copied back to the host."""
+    library every call; the results -- loss, dL/dtheta, dL/dPhat, dL/dproj
+    and the updated motion and Adam state -- copied back to the host.  Only
+    the volume and dL/dvol, intermediates of the step, stay on the device."""
     import torch
 
     from paper_2401_09283_gb300 import bp
@@ -473,7 +479,7 @@ def e2e_leg(args, cfg, P, proj, vw, geo, dev):
     loss_h = torch.empty((), dtype=torch.float64).pin_memory()
     vol = torch.empty(cfg.vol_shape, dtype=torch.float32, device=dev)
     dvol = torch.empty_like(vol)
-    g_D = torch.empty(proj.shape, dtype=torch.float32, device=dev)
+    g_D = torch.empty(proj.shape, dtype=torch.float32).pin_memory()
     it = [0]
 
     def step():
@@ -496,7 +502,8 @@ def e2e_leg(args, cfg, P, proj, vw, geo, dev):
     pb = proj.numel() * 4
     small_in = (V * 12 + V * 6 + V) * 8
     h2d = 2 * (pb + small_in) + 3 * V * 6 * 8            # fwd + vjp copies, adam state in
-    d2h = 8 + (V * 6 + V * 12) * 8 + 3 * V * 6 * 8        # loss, dL/dtheta, dL/dPhat, adam out
+    # loss, dL/dtheta, dL/dPhat, dL/dproj, adam state out
+    d2h = 8 + (V * 6 + V * 12) * 8 + g_D.numel() * 4 + 3 * V * 6 * 8
     return {"value": PASSES * cfg.voxel_views * n / dt, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": dt / n * 1e3, "steps": n}

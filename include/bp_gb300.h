@@ -171,8 +171,10 @@ int bp_tv(bp_ctx* ctx, const float* vol, const bp_vol_desc* vdesc, double eps, d
  * callers that cannot allocate device memory during the call -- code being
  * recorded into a CUDA graph (an allocation would break the stream capture),
  * hosts that give all device memory to their own pool at start-up, and
- * real-time loops that must not wait on the allocator.  It computes exactly
- * what bp_sharpness computes, needs no context, allocates nothing (no
+ * real-time loops that must not wait on the allocator.  It computes the loss
+ * and gradient of bp_sharpness -- the gradient bit for bit, the loss up to
+ * the order of its FP64 sums (fixed chunks of 4096 voxels here, a
+ * grid-stride loop there) -- needs no context, allocates nothing (no
  * cudaMalloc/cudaFree, no allocating library routine) and keeps its per-chunk
  * FP64 partial sums in a fixed array inside the library: 256 KiB on every GPU
  * that loads the library, held until the process exits.

@@ -27,6 +27,17 @@ def scan_case(name: str, views=None, device="cpu"):
     return cfg, P, th, proj, delta
 
 
+# Storage tolerances of the volume against the oracle on the FP32 data.  FP16
+# uses the bound the specification states (2e-3).  BF16 has none stated; its
+# bound is its unit roundoff 2^-9 (8 stored mantissa bits, round to nearest):
+# the per-element relative error of the stored data is below it, and on c3
+# the volume's rel-L2 came to 0.28 of the unit roundoff for both formats
+# (FP16 6.5e-5 of 2^-12, BF16 5.4e-4 of 2^-9), so a storage or conversion
+# fault of a few times the measured error fails.
+FP16_STORAGE_TOL = 2e-3
+BF16_STORAGE_TOL = 2.0 ** -9
+
+
 def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
@@ -45,3 +56,21 @@ def random_case(seed, shape=(19, 21, 37), views=7, nu=40, nv=30, pitch=3.0, spac
     delta = rng.standard_normal(shape).astype(np.float32)
     origin = tuple(-(n - 1) / 2.0 * spacing for n in shape[::-1])
     return cfg, P, th, proj, delta, origin
+
+
+def per_view_worst(g, o, floor=1e-2):
+    """Worst per-view relative error of a motion gradient (V,6) or (V,3,4):
+    max over views j of ||g_j - o_j|| / ||o_j||, over the views whose
+    oracle gradient is not negligible (||o_j|| >= floor * max_j ||o_j||);
+    views below the floor carry little of the gradient and their relative
+    error measures cancellation, not the kernel."""
+    g = np.asarray(g, np.float64).reshape(len(g), -1)
+    o = np.asarray(o, np.float64).reshape(len(o), -1)
+    no = np.linalg.norm(o, axis=1)
+    keep = no >= floor * no.max()
+    return float(np.max(np.linalg.norm(g - o, axis=1)[keep] / no[keep]))
+
+
+def motion_errors(g, o):
+    """(rel-L2 translations, rel-L2 rotations, worst per-view relative error)."""
+    return (rel_l2(g[:, :3], o[:, :3]), rel_l2(g[:, 3:], o[:, 3:]), per_view_worst(g, o))

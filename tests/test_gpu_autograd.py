@@ -59,6 +59,26 @@ def test_gradcheck_motion_c4g():
                                     nondet_tol=1e-6)
 
 
+def test_gradcheck_projections_c4g():
+    """torch.autograd.gradcheck over the projections on the c4g instance, in
+    full (non-fast) mode: every one of the 12 x 24 x 32 inputs against every
+    output voxel.  The backprojection is linear in the data, so a central
+    difference with eps = 1 has no truncation error and its only error is
+    the FP32 rounding of the two forwards (about 1e-7 absolute on values of
+    order 1); the Jacobian entries are bilinear weights times c_j (sid/w)^2,
+    at most about 0.3.  Tolerances: 1e-5 absolute plus 1e-4 relative.  The
+    data VJP sums with FP32 atomics, so two backward passes may differ in
+    the last bits (nondet_tol)."""
+    cfg, P, th, proj, _, args = setup("c4g")
+    p64 = proj.double().clone().requires_grad_(True)
+
+    def f(p):
+        return backproject(p.float(), th, P, deriv="exact", **args).double()
+
+    assert torch.autograd.gradcheck(f, (p64,), eps=1.0, atol=1e-5, rtol=1e-4, fast_mode=False,
+                                    nondet_tol=1e-6)
+
+
 @pytest.mark.slow
 def test_fd_24_motion_parameters_c4():
     """Config 4 (192^3, 180 views, 320x240): the autograd gradient of

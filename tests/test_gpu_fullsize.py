@@ -12,7 +12,7 @@ import pytest
 import torch
 
 import oracle
-from cases import rel_l2, scan_case
+from cases import BF16_STORAGE_TOL, FP16_STORAGE_TOL, motion_errors, rel_l2, scan_case
 from paper_2401_09283_gb300 import bp
 from paper_2401_09283_gb300 import workloads as W
 
@@ -61,12 +61,14 @@ def test_c2_full_size_sampled():
                            cfg.sid)
     om = oracle.chain_motion(P[views], th[views], oP)
     assert rel_l2(gP[views], oP) <= 1e-3
-    for sl in (slice(0, 3), slice(3, 6)):
-        assert rel_l2(gm[views][:, sl], om[:, sl]) <= 1e-3
+    errs = motion_errors(gm[views], om)
+    print("c2 motion gradient: rel-L2 translations %.3g, rotations %.3g, worst view %.3g" % errs)
+    assert max(errs) <= 1e-3
     assert rel_l2(gD[views], oD) <= 1e-5
 
 
-@pytest.mark.parametrize("dtype,tol", [(torch.float16, 2e-3), (torch.bfloat16, 3.2e-2)])
+@pytest.mark.parametrize("dtype,tol", [(torch.float16, FP16_STORAGE_TOL),
+                                       (torch.bfloat16, BF16_STORAGE_TOL)])
 def test_c3_half_storage_sampled(dtype, tol):
     rng = np.random.default_rng(3)
     cfg = W.C3
@@ -105,6 +107,7 @@ def test_c3_half_storage_sampled(dtype, tol):
                           want_proj=False)
     om = oracle.chain_motion(P, th, oP)
     g = gm.cpu().numpy()
-    errs = [rel_l2(g[:, sl], om[:, sl]) for sl in (slice(0, 3), slice(3, 6))]
-    print("c3 %s motion gradient rel-L2 (translations, rotations): %.3g, %.3g" % (dtype, *errs))
+    errs = motion_errors(g, om)
+    print("c3 %s motion gradient: rel-L2 translations %.3g, rotations %.3g, worst view %.3g"
+          % ((dtype,) + errs))
     assert max(errs) <= 1e-3

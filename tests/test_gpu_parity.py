@@ -4,15 +4,16 @@ same seeded inputs.
 Tolerances (stated by the benchmark spec, or derived in the design
 notes): volumes rel-L2 <= 1e-5 for FP32 data; motion gradients rel-L2
 <= 1e-3 per parameter group (translations, rotations); FP16-stored data
-rel-L2 <= 2e-3 against the oracle on the FP32 data; BF16 <= 3.2e-2 (16x the
-FP16 bound: the ratio of the two formats' unit roundoffs).
+rel-L2 <= 2e-3 against the oracle on the FP32 data; BF16 <= 2^-9, its unit
+roundoff (derivation beside BF16_STORAGE_TOL in cases.py).
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle
-from cases import rel_l2, random_case, scan_case
+from cases import (BF16_STORAGE_TOL, FP16_STORAGE_TOL, motion_errors, per_view_worst, rel_l2,
+                   random_case, scan_case)
 from paper_2401_09283_gb300 import bp
 from paper_2401_09283_gb300 import workloads as W
 
@@ -87,7 +88,9 @@ def test_c1_vjp(weight, deriv):
     om = oracle.chain_motion(P, th, oP)
     # all three products: the data VJP runs fused into the motion-VJP kernel
     gm, gP, gD = gpu_vjp(delta, proj, P, th, cfg.spacing3, cfg.origin, vw, weight, deriv, cfg.sid)
-    assert motion_rel(gm, om) <= GRAD_TOL
+    errs = motion_errors(gm, om)
+    print("c1 %s %s motion gradient: rel-L2 %.3g / %.3g, worst view %.3g" % ((weight, deriv) + errs))
+    assert max(errs) <= GRAD_TOL
     assert rel_l2(gP, oP) <= GRAD_TOL
     assert rel_l2(gD, oD) <= VOL_TOL
     # each product alone: the unfused kernels
@@ -251,7 +254,8 @@ def test_strided_projections():
 
 # ---------------------------------------------------------- reduced precision
 
-@pytest.mark.parametrize("dtype,tol", [(torch.float16, 2e-3), (torch.bfloat16, 3.2e-2)])
+@pytest.mark.parametrize("dtype,tol", [(torch.float16, FP16_STORAGE_TOL),
+                                       (torch.bfloat16, BF16_STORAGE_TOL)])
 def test_c1_half_storage(dtype, tol):
     cfg, P, th, proj, delta = scan_case("c1")
     vw = np.full(cfg.views, cfg.delta_beta)

@@ -122,3 +122,18 @@ def test_rpe_zero_and_tz_closed_form():
     depth = np.einsum("vk,pk->vp", P[:, 2, :], ph)
     want = np.mean(s * cfg.sdd / depth)
     assert abs(got - want) < 1e-10 * want
+
+
+def test_reprojection_error_of_the_package_equals_the_oracle():
+    """metrics.reprojection_error (the RPE every reported number uses) against
+    the oracle's RPE of Sec. IV-A on moved geometries of two configs."""
+    from paper_2401_09283_gb300.metrics import reprojection_error
+    pts = W.rpe_points()
+    for cfg in (W.C2, W.PAPER):
+        P = W.projection_matrices(cfg)
+        Pm = oracle.compose(P, W.motion_curves(cfg))
+        want = oracle.rpe(P, Pm, pts, cfg.pitch, cfg.pitch)
+        got = reprojection_error(P, Pm, pts, cfg.pitch, cfg.pitch)
+        assert want > 0.5
+        assert abs(got - want) <= 1e-12 * want
+        assert reprojection_error(Pm, Pm, pts, cfg.pitch, cfg.pitch) == 0.0

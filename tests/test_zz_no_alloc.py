@@ -1,6 +1,8 @@
 """bp_sharpness_noalloc: the allocation-free entry point, for callers that
 cannot allocate device memory during a call (graph capture, pooled or
-real-time hosts).  It must give what bp_sharpness gives.
+real-time hosts).  It must give the oracle's sharpness loss and gradient,
+and what bp_sharpness gives: the gradient bit for bit (same per-voxel
+arithmetic), the loss up to the order of its FP64 sums.
 
 Collected last on purpose (file name), so that a run stopping at the first
 failure has run every other test before it.  It also passes alone in a fresh
@@ -16,6 +18,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover - GPU machine only
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
+import oracle  # noqa: E402
 from paper_2401_09283_gb300 import bp, native  # noqa: E402
 
 DEV = torch.device("cuda:0")
@@ -43,9 +46,15 @@ def test_noalloc_matches_bp_sharpness_on_two_calls():
         L_ref, g_ref = bp.bp_sharpness(vol)
         L, g = noalloc(vol)
         torch.cuda.synchronize()
-        assert abs(float(L) - float(L_ref)) <= 1e-6 * abs(float(L_ref))
         gr, gg = g_ref.cpu().numpy(), g.cpu().numpy()
-        assert np.abs(gg - gr).max() <= 1e-5 * np.abs(gr).max()
+        assert np.array_equal(gg, gr)
+        assert abs(float(L) - float(L_ref)) <= 1e-12 * abs(float(L_ref))
+        # against the FP64 oracle: the kernels round each difference to FP32
+        # (relative 2^-24, squared in FP64) and sum the six differences of
+        # the gradient in FP32
+        Lo, go = oracle.sharpness(vol.cpu().numpy().astype(np.float64))
+        assert abs(float(L) - Lo) <= 1e-6 * abs(Lo)
+        assert np.abs(gg - go).max() <= 1e-5 * np.abs(go).max()
 
 
 def test_noalloc_rejects_bad_sizes_and_host_memory():
