@@ -280,6 +280,8 @@ def run_ours(args):
            "loss_last": float(loss)}
     if clk:
         out["clocks"] = clk
+    if not args.quick:
+        out["probes"] = probe_leg(local, sms, clk)
 
     if not args.no_e2e and not args.quick:
         out["e2e"] = e2e_leg(args, cfg, P, proj, vw, geo, dev)
@@ -290,14 +292,7 @@ def run_ours(args):
     if not args.quick and not args.no_c3 and rank == 0:
         out["precision_form"] = precision_leg(args, dev)
     if not args.quick and args.serving > 0 and rank == 0:
-        from paper_2401_09283_gb300 import serving as S
-        reqs = S.make_requests(args.serving, 4.0, 5, "fp16", device=local)
-        srv = S.Server(device=local, slots=4)
-        res = srv.run(reqs)
-        out["serving"] = {"served_fp16": S.summarize(res, reqs, srv)}
-        reqs32 = S.make_requests(args.serving, 4.0, 5, "fp32", device=local)
-        out["serving"]["sequential_fp32"] = S.summarize(S.run_sequential(reqs32, device=local),
-                                                        reqs32, None)
+        out["serving"] = serving_leg(args, local)
     if ws > 1:
         torch.distributed.barrier()
     if rank == 0 and not args.no_cpu and not args.quick and ws == 1:
@@ -306,6 +301,27 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def probe_leg(device, sms, clk):
+    """Measured throughputs behind the roofline's denominators (bp_probe):
+    FP32 FMA lane operations per clock per SM with scalar FFMA and with the
+    packed f32x2 FMA the kernels use (a packed instruction counts two lane
+    operations), against the 128 lanes per SM per clock of the ALU roofline;
+    and FP32 atomic adds per second in L2, coalesced and in the data VJP's
+    scattered pattern (the data VJP is the adjoint scatter of Eq. 3: four
+    atomic adds per sample unless merged)."""
+    from paper_2401_09283_gb300 import native
+    mhz = (clk or {}).get("sm_mhz") or SM_MAX_MHZ
+    vals = {k: native.probe(i, device) for i, k in enumerate(
+        ("ffma_lane_ops_per_s", "ffma2_lane_ops_per_s", "red_coalesced_per_s",
+         "red_scatter_2x2_per_s"))}
+    per_clk = lambda v: v / (sms * mhz * 1e6)
+    vals["ffma_lane_ops_per_clk_per_sm"] = per_clk(vals["ffma_lane_ops_per_s"])
+    vals["ffma2_lane_ops_per_clk_per_sm"] = per_clk(vals["ffma2_lane_ops_per_s"])
+    vals["roofline_lanes_per_clk_per_sm"] = 128
+    vals["clock_mhz_used"] = mhz
+    return vals
 
 
 def motion_estimation_leg(args, cfg, P, th_true, proj, vw, dev):
@@ -344,6 +360,19 @@ def motion_estimation_leg(args, cfg, P, th_true, proj, vw, dev):
                      "loss_first": float(hist[0]), "loss_last": float(hist[it - 1])}
     out["jobs_per_s"] = 1000.0 / (out["sharpness"]["ms_per_iter"] * args.me_iters)
     return out
+
+
+def serving_leg(args, device):
+    """Config 5: a seeded Poisson stream of motion-estimation jobs (volumes
+    128-384^3, 120-496 views, 50 iterations each) served with FP16
+    projections as one batch of resident jobs (batched persistent launches),
+    against the same jobs one at a time in plain FP32; jobs/s, p50/p99
+    latency and the final reprojection error of each form, best of
+    `serving_repeats` runs with every run's jobs/s listed, plus one run of the
+    served FP16 form without batching (per-job graphs on streams)."""
+    from paper_2401_09283_gb300 import serving as S
+    return S.compare(n_jobs=args.serving, rate=4.0, seed=5, slots=4, opt=S.OptConfig(iters=50),
+                     repeats=max(1, args.serving_repeats), device=device)
 
 
 def paper_setup_leg(args, dev):

@@ -114,6 +114,32 @@ long long bp_ctx_launch_count(const bp_ctx* ctx);
 int bp_ctx_set_timing(bp_ctx* ctx, int enable);
 int bp_ctx_timing(bp_ctx* ctx, const char* kernel, double* total_ms, long long* launches);
 
+/* Throughput probes behind the roofline figures (instrumentation; the paper
+ * has no counterpart).  *result, per second on the context's device:
+ *   kind 0  FP32 FMA lane operations with scalar FFMA;
+ *   kind 1  FP32 FMA lane operations with packed f32x2 FMA (two per lane and
+ *           instruction) -- the packed form halves the issue slots, not the
+ *           FP32 pipe's lane rate;
+ *   kind 2  FP32 atomic adds in L2, lanes of a warp on consecutive words;
+ *   kind 3  FP32 atomic adds in L2 in the data VJP's pattern (the 2 x 2 taps
+ *           of samples ~2.6 px apart).
+ * Synchronous (waits for `stream`); uses 64 MiB of context workspace. */
+int bp_probe(bp_ctx* ctx, int kind, double* result, void* stream);
+
+/* Bounds checking (debug builds).  A library compiled with -DBP_BOUNDS_CHECK
+ * (paper_2401_09283_gb300.build.build_library(variant="bounds")) checks every
+ * staged, gathered and scattered index of the backprojection kernels against
+ * the range it must lie in; a failed check sets bit `code` of a device flag
+ * word (0 staged tap, 1 global tap, 2 scatter, 3 staging destination, 7 self
+ * test), records the first failure (*first_failure = code << 56 | a << 28 | b,
+ * the two offending coordinates; -1 when none), and redirects the access to
+ * a safe position -- nothing traps and nothing outside the buffers is
+ * touched.  op: 0 read, 1 read and clear, 2 record a synthetic failure first
+ * (tests the reporting path without touching memory).  Synchronises the
+ * device's legacy default stream.  Release builds return BP_ERR_UNSUPPORTED.
+ * The paper has no counterpart (a debugging aid). */
+int bp_bounds_check(bp_ctx* ctx, int op, unsigned int* flags, long long* first_failure);
+
 /* Eq. 1 for every view: Phat[j] = P[j] T(motion[j]) (float64, [V][12]).
  * motion may be NULL (identity; Phat is then P bit for bit). */
 int bp_compose(bp_ctx* ctx, int nviews, const double* P, const double* motion, double* Phat,
@@ -308,6 +334,48 @@ const float* bp_job_volume(const bp_job* job);
 /* Waits for the job's queued iterations, then frees its memory with the
  * stream-ordered allocator (no device-wide synchronisation). */
 void bp_job_destroy(bp_job* job);
+
+/* Cancel a job: later motion_step calls return BP_ERR_CANCELLED and a batch
+ * drops it at its next step; iterations already queued still run, and the
+ * job's state stays readable (bp_job_get_motion) until bp_job_destroy.  The
+ * paper has no counterpart (serving control). */
+int bp_job_cancel(bp_job* job);
+/* Wait for the job's queued iterations for at most timeout_ms milliseconds
+ * (< 0: no limit), polling an event from the host; BP_ERR_TIMEOUT if they
+ * are still running then (nothing is stopped; wait again or cancel).  The
+ * paper has no counterpart (serving control). */
+int bp_job_wait(const bp_job* job, double timeout_ms);
+/* Iterations queued for the job so far (motion_step or batches), or -1. */
+int bp_job_iterations_queued(const bp_job* job);
+
+/* ---------------------------------------------------------------- batches
+ * Several resident jobs advanced together (the serving form): each stage of
+ * an iteration -- compose (Eq. 1), backprojection (Eq. 3), loss, motion VJP
+ * (Eqs. 4-5), FP64 reduction and chain (Eq. 2), update -- is ONE persistent
+ * launch whose blocks walk the work items (views, tiles, (tile, view chunk)
+ * pairs, loss chunks) of every member, so jobs of different volume and view
+ * counts share each kernel and fill the GPU together.  The kernels read the
+ * member set from a device table; one CUDA graph, captured at the first step,
+ * serves every later member set.  Every item runs the per-job arithmetic:
+ * a member's iterations are bit for bit those of motion_step.
+ * Members must share dtype, weight, derivative mode, loss and optimiser,
+ * use per-view motion (motion_nodes = 0) and have detector rows of a
+ * multiple of 16 bytes; a job is a member of at most one batch and is not
+ * advanced by motion_step while it is one.  The paper has no counterpart. */
+typedef struct bp_batch bp_batch;
+/* max_jobs: 1..64 members. */
+int bp_batch_create(bp_ctx* ctx, int max_jobs, bp_batch** out);
+/* Replace the member set (n_jobs = 0 empties it); takes effect at the next
+ * step.  BP_ERR_INVALID_ARG / BP_ERR_UNSUPPORTED / BP_ERR_CANCELLED for a
+ * member that breaks the rules above; the set is then unchanged. */
+int bp_batch_set_jobs(bp_batch* batch, bp_job* const* jobs, int n_jobs);
+/* Queue n_iters iterations of every member on `stream` (asynchronous; waits
+ * for the members' earlier work; cancelled members are dropped first). */
+int bp_batch_step(bp_batch* batch, int n_iters, void* stream);
+/* Number of members, or -1. */
+int bp_batch_size(const bp_batch* batch);
+/* Waits for the batch's queued steps, then frees it (the jobs stay). */
+void bp_batch_destroy(bp_batch* batch);
 
 #ifdef __cplusplus
 }

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbp_gb300.so")
 SOURCES = ["bp_api.cu", "bp_job.cu", "bp_geom.cu", "bp_project.cu", "bp_noalloc.cu", "bp_spline.cu",
-           "bp_fdk.cu"]
+           "bp_fdk.cu", "bp_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -33,24 +33,33 @@ def _flags(extra=()):
                    "-I", os.path.join(ROOT, "include"), "-I", CSRC] + list(extra)
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+# Variants: the release library, and a debug library with every gather and
+# scatter index checked (-DBP_BOUNDS_CHECK; bp_bounds_check reports failures).
+VARIANTS = {"release": (BUILD, LIB, []),
+            "bounds": (os.path.join(HERE, "_build_bc"),
+                       os.path.join(HERE, "_build_bc", "libbp_gb300_bc.so"),
+                       ["-DBP_BOUNDS_CHECK"])}
+
+
+def _stale(lib=LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     deps.append(os.path.join(ROOT, "include", "bp_gb300.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build_library(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build_library(force: bool = False, verbose: bool = False, extra=(), variant="release") -> str:
+    build_dir, lib, vflags = VARIANTS[variant]
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + _flags(extra)
+        obj = os.path.join(build_dir, os.path.splitext(src)[0] + ".o")
+        cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + _flags(list(vflags) + list(extra))
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))
@@ -60,13 +69,13 @@ def build_library(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with concurrent.futures.ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [cc, "-shared"] + ARCH + ["-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

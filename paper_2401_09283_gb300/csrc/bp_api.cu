@@ -138,7 +138,7 @@ void bp_ctx_destroy(bp_ctx* ctx) {
                  &ctx->s_P,    &ctx->s_motion, &ctx->s_vw,     &ctx->s_scale,    &ctx->s_vol,
                  &ctx->s_dvol, &ctx->s_out_motion, &ctx->s_out_P, &ctx->s_out_proj,
                  &ctx->s_theta, &ctx->s_grad, &ctx->s_m1,       &ctx->s_m2,       &ctx->s_loss,
-                 &ctx->s_nodes, &ctx->s_out_nodes};
+                 &ctx->s_nodes, &ctx->s_out_nodes, &ctx->probe};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   resolve_timing(ctx);
@@ -155,7 +155,7 @@ long long bp_ctx_workspace_bytes(const bp_ctx* ctx) {
                        &ctx->s_P,    &ctx->s_motion, &ctx->s_vw,     &ctx->s_scale,    &ctx->s_vol,
                        &ctx->s_dvol, &ctx->s_out_motion, &ctx->s_out_P, &ctx->s_out_proj,
                        &ctx->s_theta, &ctx->s_grad, &ctx->s_m1,       &ctx->s_m2,       &ctx->s_loss,
-                       &ctx->s_nodes, &ctx->s_out_nodes};
+                       &ctx->s_nodes, &ctx->s_out_nodes, &ctx->probe};
   long long t = 0;
   for (const Buf* b : bufs) t += (long long)b->n;
   return t;
@@ -187,6 +187,31 @@ int bp_ctx_timing(bp_ctx* ctx, const char* kernel, double* total_ms, long long* 
 }
 
 long long bp_ctx_launch_count(const bp_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int bp_probe(bp_ctx* ctx, int kind, double* result, void* stream) {
+  if (!ctx || !result || kind < 0 || kind > 3) return BP_ERR_INVALID_ARG;
+  ctx->err.clear();
+  DeviceGuard g(ctx->device);
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "bp_probe");
+  const long long words = 16LL << 20;  // 64 MiB of scratch for the atomics
+  CK(ensure(ctx->probe, (size_t)words * 4), "bp_probe: scratch");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(ctx->probe.p, 0, (size_t)words * 4, s), "bp_probe: clear");
+  CK(bpk::run_probe(kind, (float*)ctx->probe.p, words, sms, result, s), "bp_probe");
+  return BP_OK;
+}
+
+int bp_bounds_check(bp_ctx* ctx, int op, unsigned int* flags, long long* first_failure) {
+  if (!ctx || !flags || !first_failure || op < 0 || op > 2) return BP_ERR_INVALID_ARG;
+  ctx->err.clear();
+  DeviceGuard g(ctx->device);
+  const cudaError_t e = bpk::bounds_status(flags, first_failure, op, nullptr);
+  if (e == cudaErrorNotSupported)
+    return fail(ctx, BP_ERR_UNSUPPORTED, "bp_bounds_check: library built without BP_BOUNDS_CHECK");
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_bounds_check");
+  return BP_OK;
+}
 
 int bp_compose(bp_ctx* ctx, int nviews, const double* P, const double* motion, double* Phat,
                void* stream) {

@@ -47,13 +47,11 @@ __device__ static void p_times_rigid(const double* P, const double R[9], const d
   }
 }
 
-// One thread per view: Phat = P T(theta) (Eq. 1), then P' = Phat A.
-__global__ void compose_kernel(const double* __restrict__ P, const double* __restrict__ theta,
-                               const double* __restrict__ vw, const float* __restrict__ vscale,
-                               int V, int fdk, double sid, VolInfo vi, ViewGeom* __restrict__ geom,
-                               double* __restrict__ Phat) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= V) return;
+// View j: Phat = P T(theta) (Eq. 1), then P' = Phat A.
+__device__ static void compose_view(const double* __restrict__ P, const double* __restrict__ theta,
+                                    const double* __restrict__ vw, const float* __restrict__ vscale,
+                                    int fdk, double sid, const VolInfo& vi,
+                                    ViewGeom* __restrict__ geom, double* __restrict__ Phat, int j) {
   double Ph[12];
   if (theta) {
     double R[9];
@@ -80,6 +78,16 @@ __global__ void compose_kernel(const double* __restrict__ P, const double* __res
   geom[j] = g;
 }
 
+// One thread per view.
+__global__ void compose_kernel(const double* __restrict__ P, const double* __restrict__ theta,
+                               const double* __restrict__ vw, const float* __restrict__ vscale,
+                               int V, int fdk, double sid, VolInfo vi, ViewGeom* __restrict__ geom,
+                               double* __restrict__ Phat) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= V) return;
+  compose_view(P, theta, vw, vscale, fdk, sid, vi, geom, Phat, j);
+}
+
 cudaError_t launch_compose(const double* P, const double* theta, const double* view_weight,
                            const float* view_scale, int V, int fdk, double sid,
                            const VolInfo& vi, ViewGeom* geom, double* Phat, cudaStream_t s) {
@@ -95,11 +103,13 @@ cudaError_t launch_compose(const double* P, const double* theta, const double* v
 // (each record is in its tile's anchored, centred frame and is mapped back to
 // the index frame first), then dL/dPhat = dL/dP' A^T and
 // dL/dtheta_m = < dL/dPhat , P dT/dtheta_m > (Eq. 2 through Eq. 1).
-__global__ void reduce_chain_kernel(const float* __restrict__ partials, int ntiles, VolInfo vi,
-                                    const double* __restrict__ P, const double* __restrict__ theta,
-                                    int V, double* __restrict__ dPhat, double* __restrict__ dth) {
+// All 256 threads of the block call it for view j.
+__device__ static void reduce_chain_view(const float* __restrict__ partials, int ntiles,
+                                         const VolInfo& vi, const double* __restrict__ P,
+                                         const double* __restrict__ theta,
+                                         double* __restrict__ dPhat, double* __restrict__ dth,
+                                         int j) {
   __shared__ double red[12][256];
-  const int j = blockIdx.x;
   const int tid = threadIdx.x;
   double acc[12];
   for (int e = 0; e < 12; ++e) acc[e] = 0.0;
@@ -162,6 +172,12 @@ __global__ void reduce_chain_kernel(const float* __restrict__ partials, int ntil
   }
 }
 
+__global__ void reduce_chain_kernel(const float* __restrict__ partials, int ntiles, VolInfo vi,
+                                    const double* __restrict__ P, const double* __restrict__ theta,
+                                    int V, double* __restrict__ dPhat, double* __restrict__ dth) {
+  reduce_chain_view(partials, ntiles, vi, P, theta, dPhat, dth, blockIdx.x);
+}
+
 cudaError_t launch_reduce_chain(const float* partials, int ntiles, const VolInfo& vi,
                                 const double* P, const double* theta, int V, double* dL_dPhat,
                                 double* dL_dtheta, cudaStream_t s) {
@@ -184,16 +200,19 @@ int sharpness_blocks(long long nvox) {
 // L = -(1/K) sum_pairs (I[y]-I[x])^2 over forward neighbours y = x + e_a
 // inside the volume; dL/dI[x] = (2/K) sum over the valid neighbours n of x
 // (I[n] - I[x]).  Per-block FP64 partial sums in a fixed order.
-__global__ void sharpness_kernel(const float* __restrict__ vol, int nx, int ny, int nz,
-                                 double* __restrict__ block_sums, float* __restrict__ grad) {
+// Block b of nb (grid-stride partition of the voxels over nb blocks of
+// SH_THREADS threads); all threads of the block call it.
+__device__ static void sharpness_block(const float* __restrict__ vol, int nx, int ny, int nz,
+                                       double* __restrict__ block_sums, float* __restrict__ grad,
+                                       int b, int nb) {
   __shared__ double red[SH_THREADS];
   const long long nvox = (long long)nx * ny * nz;
   const double K = (double)nvox;
   const float g2 = (float)(2.0 / K);
   double acc = 0.0;
   const long long nxy = (long long)nx * ny;
-  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < nvox;
-       x += (long long)gridDim.x * blockDim.x) {
+  for (long long x = b * (long long)SH_THREADS + threadIdx.x; x < nvox;
+       x += (long long)nb * SH_THREADS) {
     int i = (int)(x % nx);
     int j = (int)((x / nx) % ny);
     int k = (int)(x / nxy);
@@ -227,7 +246,12 @@ __global__ void sharpness_kernel(const float* __restrict__ vol, int nx, int ny, 
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) block_sums[blockIdx.x] = red[0];
+  if (threadIdx.x == 0) block_sums[b] = red[0];
+}
+
+__global__ void sharpness_kernel(const float* __restrict__ vol, int nx, int ny, int nz,
+                                 double* __restrict__ block_sums, float* __restrict__ grad) {
+  sharpness_block(vol, nx, ny, nz, block_sums, grad, blockIdx.x, gridDim.x);
 }
 
 __global__ void sharpness_finish_kernel(const double* __restrict__ block_sums, int nb, double K,
@@ -321,9 +345,11 @@ cudaError_t launch_adam(int V, double* theta, const double* grad, double* m1, do
 // numbers live on the device: the loss goes to history[*iter], the update
 // reads *iter and advances it.
 
-__global__ void sharpness_finish_hist_kernel(const double* __restrict__ block_sums, int nb,
-                                             double K, double* __restrict__ history,
-                                             const int* __restrict__ iter, int hist_len) {
+// Fixed-order sum of nb block sums -> -sum/K at history[*iter] (TV: +sum/K,
+// sign = +1).  All SH_THREADS threads of the block call it.
+__device__ static void loss_finish_hist(const double* __restrict__ block_sums, int nb, double K,
+                                        double sign, double* __restrict__ history,
+                                        const int* __restrict__ iter, int hist_len) {
   __shared__ double red[SH_THREADS];
   double acc = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += block_sums[b];
@@ -335,8 +361,14 @@ __global__ void sharpness_finish_hist_kernel(const double* __restrict__ block_su
   }
   if (threadIdx.x == 0) {
     const int it = *iter;
-    if (it >= 0 && it < hist_len) history[it] = -red[0] / K;
+    if (it >= 0 && it < hist_len) history[it] = sign * red[0] / K;
   }
+}
+
+__global__ void sharpness_finish_hist_kernel(const double* __restrict__ block_sums, int nb,
+                                             double K, double* __restrict__ history,
+                                             const int* __restrict__ iter, int hist_len) {
+  loss_finish_hist(block_sums, nb, K, -1.0, history, iter, hist_len);
 }
 
 cudaError_t launch_sharpness_hist(const float* vol, int nx, int ny, int nz, double* block_sums,
@@ -355,9 +387,9 @@ cudaError_t launch_sharpness_hist(const float* vol, int nx, int ny, int nz, doub
 
 // Adam with separate step sizes for translations (mm) and rotations (rad);
 // n = *iter + 1.
-__global__ void adam_dev_kernel(int V, double* theta, const double* grad, double* m1, double* m2,
-                                double lr_t, double lr_r, double b1, double b2, double eps,
-                                int* iter, int gauge) {
+__device__ static void adam_dev_body(int V, double* theta, const double* grad, double* m1,
+                                     double* m2, double lr_t, double lr_r, double b1, double b2,
+                                     double eps, int* iter, int gauge) {
   const int n = *iter + 1;
   const double c1 = 1.0 - pow(b1, (double)n), c2 = 1.0 - pow(b2, (double)n);
   for (int e = threadIdx.x; e < 6 * V; e += blockDim.x) {
@@ -374,10 +406,16 @@ __global__ void adam_dev_kernel(int V, double* theta, const double* grad, double
   if (threadIdx.x == 0) *iter = n;
 }
 
+__global__ void adam_dev_kernel(int V, double* theta, const double* grad, double* m1, double* m2,
+                                double lr_t, double lr_r, double b1, double b2, double eps,
+                                int* iter, int gauge) {
+  adam_dev_body(V, theta, grad, m1, m2, lr_t, lr_r, b1, b2, eps, iter, gauge);
+}
+
 // Eq. 6 with step s0 * t^n (n = *iter, starting at 0), separate s0 for
 // translations and rotations.
-__global__ void gd_dev_kernel(int V, double* theta, const double* grad, double s0_t, double s0_r,
-                              double t, int* iter, int gauge) {
+__device__ static void gd_dev_body(int V, double* theta, const double* grad, double s0_t,
+                                   double s0_r, double t, int* iter, int gauge) {
   const int n = *iter;
   const double f = pow(t, (double)n);
   for (int e = threadIdx.x; e < 6 * V; e += blockDim.x)
@@ -385,6 +423,11 @@ __global__ void gd_dev_kernel(int V, double* theta, const double* grad, double s
   __syncthreads();
   if (gauge) remove_mean(V, theta);
   if (threadIdx.x == 0) *iter = n + 1;
+}
+
+__global__ void gd_dev_kernel(int V, double* theta, const double* grad, double s0_t, double s0_r,
+                              double t, int* iter, int gauge) {
+  gd_dev_body(V, theta, grad, s0_t, s0_r, t, iter, gauge);
 }
 
 cudaError_t launch_adam_dev(int V, double* theta, const double* grad, double* m1, double* m2,
@@ -419,21 +462,25 @@ __device__ __forceinline__ void tv_terms(const float* vol, long long x, long lon
   gx = vol[x + 1] - c;
   gy = vol[x + nx] - c;
   gz = vol[x + nxy] - c;
-  n = sqrt((double)gx * gx + (double)gy * gy + (double)gz * gz + (double)eps2);
-  inv_n = (float)(1.0 / n);
+  // FP32 norm (GB300's FP64 square root and division are far slower than
+  // the whole memory-bound pass); the loss sums the norms in FP64
+  const float nf = sqrtf(fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, eps2))));
+  inv_n = 1.0f / nf;
+  n = (double)nf;
 }
 
-template <bool HIST>
-__global__ void tv_kernel(const float* __restrict__ vol, int nx, int ny, int nz, float eps,
-                          double* __restrict__ block_sums, float* __restrict__ grad) {
+// Block b of nb, like sharpness_block.
+__device__ static void tv_block(const float* __restrict__ vol, int nx, int ny, int nz, float eps,
+                                double* __restrict__ block_sums, float* __restrict__ grad, int b,
+                                int nb) {
   __shared__ double red[SH_THREADS];
   const long long nvox = (long long)nx * ny * nz;
   const long long nxy = (long long)nx * ny;
   const float invK = (float)(1.0 / (double)nvox);
   const float eps2 = eps * eps;
   double acc = 0.0;
-  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < nvox;
-       x += (long long)gridDim.x * blockDim.x) {
+  for (long long x = b * (long long)SH_THREADS + threadIdx.x; x < nvox;
+       x += (long long)nb * SH_THREADS) {
     const int i = (int)(x % nx), j = (int)((x / nx) % ny), k = (int)(x / nxy);
     float gsum = 0.0f, gx, gy, gz, in;
     double n;
@@ -464,7 +511,12 @@ __global__ void tv_kernel(const float* __restrict__ vol, int nx, int ny, int nz,
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) block_sums[blockIdx.x] = red[0];
+  if (threadIdx.x == 0) block_sums[b] = red[0];
+}
+
+__global__ void tv_kernel(const float* __restrict__ vol, int nx, int ny, int nz, float eps,
+                          double* __restrict__ block_sums, float* __restrict__ grad) {
+  tv_block(vol, nx, ny, nz, eps, block_sums, grad, blockIdx.x, gridDim.x);
 }
 
 // loss = +sum/K (TV is minimised as is); with a history, at history[*iter].
@@ -496,10 +548,105 @@ cudaError_t launch_tv(const float* vol, int nx, int ny, int nz, float eps, doubl
   long long nvox = (long long)nx * ny * nz;
   int nb = sharpness_blocks(nvox);
   if (nb > max_blocks) nb = max_blocks;
-  tv_kernel<false><<<nb, SH_THREADS, 0, s>>>(vol, nx, ny, nz, eps, block_sums, grad);
+  tv_kernel<<<nb, SH_THREADS, 0, s>>>(vol, nx, ny, nz, eps, block_sums, grad);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   tv_finish_kernel<<<1, SH_THREADS, 0, s>>>(block_sums, nb, (double)nvox, loss, iter, hist_len);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- batches
+// The per-job kernels above, as launches over the work items of every member
+// of a batch table (grid-stride loops, so any grid size covers any member
+// set).  Each item runs exactly the per-job arithmetic: a job gives bit for
+// bit the same iteration in a batch as alone.
+
+__global__ void batch_compose_kernel(BatchTable* __restrict__ t, int fdk) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // the work counters of this iteration
+    t->next_fwd = 0u;
+    t->next_vjp = 0u;
+  }
+  const int n = t->njobs, total = t->off_view[n];
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
+    const int j = batch_find(t->off_view, n, w);
+    const BatchJob& J = t->job[j];
+    compose_view(J.P, J.theta, J.vw, J.scale, fdk, J.sid, J.vi, J.geom, nullptr,
+                 w - t->off_view[j]);
+  }
+}
+
+template <int LOSS>
+__global__ void batch_loss_kernel(const BatchTable* __restrict__ t) {
+  const int n = t->njobs, total = t->off_loss[n];
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int j = batch_find(t->off_loss, n, w);
+    const BatchJob& J = t->job[j];
+    const int b = w - t->off_loss[j];
+    if (LOSS == 1)
+      tv_block(J.vol, J.vi.nx, J.vi.ny, J.vi.nz, J.tv_eps, J.blk, J.dvol, b, J.nblk);
+    else
+      sharpness_block(J.vol, J.vi.nx, J.vi.ny, J.vi.nz, J.blk, J.dvol, b, J.nblk);
+    __syncthreads();
+  }
+}
+
+template <int LOSS>
+__global__ void batch_loss_finish_kernel(const BatchTable* __restrict__ t) {
+  for (int j = blockIdx.x; j < t->njobs; j += gridDim.x) {
+    const BatchJob& J = t->job[j];
+    const double K = (double)J.vi.nx * J.vi.ny * J.vi.nz;
+    loss_finish_hist(J.blk, J.nblk, K, LOSS == 1 ? 1.0 : -1.0, J.hist, J.iter, J.max_iters);
+    __syncthreads();
+  }
+}
+
+__global__ void batch_reduce_kernel(const BatchTable* __restrict__ t) {
+  const int n = t->njobs, total = t->off_view[n];
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int j = batch_find(t->off_view, n, w);
+    const BatchJob& J = t->job[j];
+    reduce_chain_view(J.partials, J.ntiles_v, J.vi, J.P, J.theta, nullptr, J.gth,
+                      w - t->off_view[j]);
+    __syncthreads();
+  }
+}
+
+template <int OPT>
+__global__ void batch_opt_kernel(const BatchTable* __restrict__ t) {
+  for (int j = blockIdx.x; j < t->njobs; j += gridDim.x) {
+    const BatchJob& J = t->job[j];
+    if (OPT == 1)
+      adam_dev_body(J.V, J.theta, J.gth, J.m1, J.m2, J.lr_t, J.lr_r, J.beta1, J.beta2, J.eps,
+                    J.iter, J.gauge);
+    else
+      gd_dev_body(J.V, J.theta, J.gth, J.lr_t, J.lr_r, J.decay, J.iter, J.gauge);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_batch_iteration(BatchTable* tab, int dtype, int fdk, int exact, int loss,
+                                   int opt, int sms, cudaStream_t s) {
+  batch_compose_kernel<<<sms, 128, 0, s>>>(tab, fdk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_batch_forward(tab, dtype, fdk, sms, s);
+  if (e != cudaSuccess) return e;
+  if (loss == 1) {
+    batch_loss_kernel<1><<<sms * 8, SH_THREADS, 0, s>>>(tab);
+    batch_loss_finish_kernel<1><<<BATCH_MAX_JOBS, SH_THREADS, 0, s>>>(tab);
+  } else {
+    batch_loss_kernel<0><<<sms * 8, SH_THREADS, 0, s>>>(tab);
+    batch_loss_finish_kernel<0><<<BATCH_MAX_JOBS, SH_THREADS, 0, s>>>(tab);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_batch_vjp(tab, dtype, fdk, exact, sms, s);
+  if (e != cudaSuccess) return e;
+  batch_reduce_kernel<<<sms * 8, 256, 0, s>>>(tab);
+  if (opt == 1)
+    batch_opt_kernel<1><<<BATCH_MAX_JOBS, 256, 0, s>>>(tab);
+  else
+    batch_opt_kernel<0><<<BATCH_MAX_JOBS, 256, 0, s>>>(tab);
   return cudaGetLastError();
 }
 

@@ -156,4 +156,89 @@ cudaError_t launch_fdk_filter(const float* raw, int V, int nv, int nu, int ext, 
                               double sid, double sdd, double arc, float* tab, float* out,
                               cudaStream_t s);
 
+// ---------------------------------------------------------------- batches
+// Several motion-estimation jobs advanced together: each stage of an
+// iteration is one launch over the work items of every member job (views,
+// tiles, (tile, view chunk) pairs, loss chunks).  The kernels read the member
+// set from a device table, so one captured graph serves any set of up to
+// BATCH_MAX_JOBS members.  Members share dtype, weight, derivative mode, loss
+// and optimiser (template or launch-uniform parameters).
+constexpr int BATCH_MAX_JOBS = 64;
+
+struct BatchJob {
+  const void* proj;        // [V][nv][nu] compact, the batch's dtype
+  const float2* grad;      // CENTRAL gradient images (NULL with BILINEAR_EXACT)
+  const double* P;         // [V][12]
+  const double* vw;        // [V] or NULL
+  const float* scale;      // [V] or NULL
+  double* theta;           // [V][6]
+  double* gth;             // [V][6]
+  double *m1, *m2;         // Adam moments
+  ViewGeom* geom;
+  float *vol, *dvol, *partials;
+  double *blk, *hist;      // loss block sums, loss history
+  int* iter;               // iterations done (device counter)
+  ProjInfo pi;
+  VolInfo vi;              // VJP tiling (zb = ZB_VJP)
+  VolInfo vif;             // forward tiling
+  double sid;
+  double lr_t, lr_r, beta1, beta2, eps, decay;
+  float tv_eps;
+  int V, ntiles_f, ntiles_v, vchunk, nblk, max_iters, gauge;
+};
+
+struct BatchTable {
+  // work counters of the two persistent stages (forward, VJP): CTAs take
+  // their next item with an atomic add, so items run in order and a CTA
+  // that drew cheap items takes more; reset by the first kernel of an
+  // iteration
+  unsigned int next_fwd, next_vjp;
+  int njobs;
+  int off_view[BATCH_MAX_JOBS + 1];  // prefix sums of V (compose, reduction)
+  int off_fwd[BATCH_MAX_JOBS + 1];   // of forward tiles
+  int off_loss[BATCH_MAX_JOBS + 1];  // of loss blocks
+  int off_vjp[BATCH_MAX_JOBS + 1];   // of VJP (tile, view chunk) items
+  BatchJob job[BATCH_MAX_JOBS];
+};
+
+// Index of the job whose range [off[j], off[j+1]) holds work item w.
+__host__ __device__ inline int batch_find(const int* off, int n, int w) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Forward tiling and VJP view chunk of a job (host side, for the table).
+int forward_zb();
+int vjp_view_chunk(const ProjInfo& pi, int dtype, int exact);
+
+// One iteration of every member: compose -> forward -> loss -> VJP ->
+// reduction and chain -> update, as persistent launches over the table's
+// work items (grids sized by the SM count, not by the members).
+// loss: 0 sharpness, 1 TV; opt: 0 Eq. 6 step, 1 Adam.
+cudaError_t prepare_batch(int dtype, int fdk, int exact);
+// The two persistent stages (bp_project.cu): SMs x resident CTAs blocks.
+cudaError_t launch_batch_forward(BatchTable* tab, int dtype, int fdk, int sms, cudaStream_t s);
+cudaError_t launch_batch_vjp(BatchTable* tab, int dtype, int fdk, int exact, int sms,
+                             cudaStream_t s);
+cudaError_t launch_batch_iteration(BatchTable* tab, int dtype, int fdk, int exact, int loss,
+                                   int opt, int sms, cudaStream_t s);
+constexpr int BATCH_KERNELS = 7;  // launches per batched iteration
+
+// Bounds-check word of debug builds (-DBP_BOUNDS_CHECK): op 0 reads the flag
+// bits and the first failure, 1 reads and clears them, 2 records a synthetic
+// failure first (self test of the reporting path).  cudaErrorNotSupported in
+// release builds.
+cudaError_t bounds_status(unsigned* flags, long long* first, int op, cudaStream_t s);
+
+// Throughput probes (bp_probe.cu): kind 0 scalar FP32 FMA lane-ops/s, 1 packed
+// f32x2 FMA lane-ops/s, 2 coalesced FP32 L2 atomic adds/s, 3 atomic adds/s in
+// the data VJP's scattered 2 x 2 pattern.  scratch: scratch_words floats.
+cudaError_t run_probe(int kind, float* scratch, long long scratch_words, int sms, double* result,
+                      cudaStream_t s);
+
 }  // namespace bpk

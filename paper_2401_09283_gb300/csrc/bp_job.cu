@@ -2,6 +2,10 @@
 // state and one captured CUDA graph per iteration of the gradient-based
 // motion estimation of Sec. II-C (compose -> backprojection -> loss -> VJP ->
 // FP64 reduction and chain rule -> optimiser update).
+#include <algorithm>
+#include <chrono>
+#include <thread>
+
 #include "bp_ctx.h"
 
 using namespace bpctx;
@@ -33,6 +37,26 @@ struct bp_job {
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  bool cancelled = false;
+  int queued = 0;               // iterations queued so far (motion_step or batches)
+  bp_batch* batch = nullptr;    // the batch this job is a member of, if any
+};
+
+struct bp_batch {
+  bp_ctx* ctx = nullptr;
+  int device = 0, sms = 0, max_jobs = 0;
+  std::vector<bp_job*> members;
+  // member configuration the captured graph was made for
+  int dtype = -1, weight = -1, deriv = -1, loss = -1, opt = -1;
+  bpk::BatchTable* host[2] = {nullptr, nullptr};  // pinned, alternating
+  cudaEvent_t host_free[2] = {nullptr, nullptr};  // copy out of host[i] done
+  int cur = 0;
+  bool dirty = true;
+  bpk::BatchTable* dev = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t last = nullptr;  // after the latest queued step
 };
 
 namespace {
@@ -326,6 +350,9 @@ int motion_step(bp_job* j, int n_iters, void* stream) {
   if (!j || n_iters < 0) return BP_ERR_INVALID_ARG;
   bp_ctx* ctx = j->ctx;
   ctx->err.clear();
+  if (j->cancelled) return fail(ctx, BP_ERR_CANCELLED, "motion_step: the job was cancelled");
+  if (j->batch)
+    return fail(ctx, BP_ERR_INVALID_ARG, "motion_step: the job is a member of a batch");
   if (n_iters == 0) return BP_OK;
   DeviceGuard g(j->device);
   if (!j->exec) {
@@ -352,6 +379,7 @@ int motion_step(bp_job* j, int n_iters, void* stream) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "motion_step: launch");
   }
   ctx->launches += (long long)kernels_per_iteration(j) * n_iters;
+  j->queued += n_iters;
   e = cudaEventRecord(j->done, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "motion_step: record");
   return BP_OK;
@@ -396,9 +424,282 @@ const float* bp_job_volume(const bp_job* j) { return j ? j->vol : nullptr; }
 void bp_job_destroy(bp_job* j) {
   if (!j) return;
   DeviceGuard g(j->device);
+  if (j->batch) {  // leave the batch: later steps no longer see this job
+    auto& m = j->batch->members;
+    m.erase(std::remove(m.begin(), m.end(), j), m.end());
+    j->batch->dirty = true;
+    j->batch = nullptr;
+  }
   j->ctx->job_bytes -= j->bytes;
   release(j);
   delete j;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ control
+
+extern "C" {
+
+int bp_job_cancel(bp_job* j) {
+  if (!j) return BP_ERR_INVALID_ARG;
+  j->cancelled = true;
+  return BP_OK;
+}
+
+int bp_job_wait(const bp_job* j, double timeout_ms) {
+  if (!j) return BP_ERR_INVALID_ARG;
+  DeviceGuard g(j->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(j->done);
+    if (e == cudaSuccess) return BP_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(j->ctx, e, "bp_job_wait");
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (timeout_ms >= 0.0 && ms >= timeout_ms)
+      return fail(j->ctx, BP_ERR_TIMEOUT,
+                  "bp_job_wait: queued iterations still running after " +
+                      std::to_string(timeout_ms) + " ms");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+int bp_job_iterations_queued(const bp_job* j) { return j ? j->queued : -1; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------- batches
+
+namespace {
+
+bool same_config(const bp_job* a, const bp_job* b) {
+  return a->pd.dtype == b->pd.dtype && a->weight == b->weight && a->deriv == b->deriv &&
+         a->opt.loss == b->opt.loss && a->opt.optimizer == b->opt.optimizer;
+}
+
+// Fill one table from the members (host side).
+void fill_table(bp_batch* b, bpk::BatchTable& T) {
+  const int n = (int)b->members.size();
+  T.njobs = n;
+  T.off_view[0] = T.off_fwd[0] = T.off_loss[0] = T.off_vjp[0] = 0;
+  const int zbf = bpk::forward_zb();
+  for (int k = 0; k < n; ++k) {
+    const bp_job* j = b->members[k];
+    bpk::BatchJob& J = T.job[k];
+    J.proj = j->proj;
+    J.grad = j->grad;
+    J.P = j->P;
+    J.vw = j->vw;
+    J.scale = j->scale;
+    J.theta = j->theta;
+    J.gth = j->gth;
+    J.m1 = j->m1;
+    J.m2 = j->m2;
+    J.geom = j->geom;
+    J.vol = j->vol;
+    J.dvol = j->dvol;
+    J.partials = j->partials;
+    J.blk = j->blk;
+    J.hist = j->hist;
+    J.iter = j->iter;
+    J.pi = j->pi;
+    J.vi = j->vi;
+    J.vif = j->vi;
+    J.vif.zb = zbf;
+    J.vif.tiles_z = (j->vd.nz + zbf - 1) / zbf;
+    J.sid = j->pd.sid;
+    J.lr_t = j->opt.lr;
+    J.lr_r = j->opt.lr_rot;
+    J.beta1 = j->opt.beta1;
+    J.beta2 = j->opt.beta2;
+    J.eps = j->opt.eps;
+    J.decay = j->opt.decay;
+    J.tv_eps = (float)j->opt.tv_eps;
+    J.V = j->pd.nviews;
+    J.ntiles_f = J.vif.tiles_x * J.vif.tiles_y * J.vif.tiles_z;
+    J.ntiles_v = j->ntiles;
+    J.vchunk = bpk::vjp_view_chunk(j->pi, j->pd.dtype, j->deriv == BP_DERIV_BILINEAR_EXACT);
+    J.nblk = j->nblk;
+    J.max_iters = j->max_iters;
+    J.gauge = j->opt.gauge;
+    const int nchunks = (J.V + J.vchunk - 1) / J.vchunk;
+    T.off_view[k + 1] = T.off_view[k] + J.V;
+    T.off_fwd[k + 1] = T.off_fwd[k] + J.ntiles_f;
+    T.off_loss[k + 1] = T.off_loss[k] + J.nblk;
+    T.off_vjp[k + 1] = T.off_vjp[k] + J.ntiles_v * nchunks;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int bp_batch_create(bp_ctx* ctx, int max_jobs, bp_batch** out) {
+  if (!ctx || !out) return BP_ERR_INVALID_ARG;
+  *out = nullptr;
+  ctx->err.clear();
+  if (max_jobs < 1 || max_jobs > bpk::BATCH_MAX_JOBS)
+    return fail(ctx, BP_ERR_INVALID_ARG,
+                "bp_batch_create: max_jobs must be 1.." + std::to_string(bpk::BATCH_MAX_JOBS));
+  DeviceGuard g(ctx->device);
+  bp_batch* b = new bp_batch();
+  b->ctx = ctx;
+  b->device = ctx->device;
+  b->max_jobs = max_jobs;
+  cudaError_t e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaMallocHost((void**)&b->host[i], sizeof(bpk::BatchTable));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->host_free[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->dev, sizeof(bpk::BatchTable));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->last, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    bp_batch_destroy(b);
+    return cuda_fail(ctx, e, "bp_batch_create");
+  }
+  *out = b;
+  return BP_OK;
+}
+
+int bp_batch_set_jobs(bp_batch* b, bp_job* const* jobs, int n_jobs) {
+  if (!b || n_jobs < 0 || (n_jobs > 0 && !jobs)) return BP_ERR_INVALID_ARG;
+  bp_ctx* ctx = b->ctx;
+  ctx->err.clear();
+  if (n_jobs > b->max_jobs)
+    return fail(ctx, BP_ERR_INVALID_ARG, "bp_batch_set_jobs: more jobs than the batch holds");
+  for (int k = 0; k < n_jobs; ++k) {
+    const bp_job* j = jobs[k];
+    if (!j) return fail(ctx, BP_ERR_INVALID_ARG, "bp_batch_set_jobs: NULL job");
+    for (int q = 0; q < k; ++q)
+      if (jobs[q] == j) return fail(ctx, BP_ERR_INVALID_ARG, "bp_batch_set_jobs: job listed twice");
+    if (j->device != b->device)
+      return fail(ctx, BP_ERR_INVALID_ARG, "bp_batch_set_jobs: job on another device");
+    if (j->cancelled) return fail(ctx, BP_ERR_CANCELLED, "bp_batch_set_jobs: cancelled job");
+    if (j->batch && j->batch != b)
+      return fail(ctx, BP_ERR_INVALID_ARG, "bp_batch_set_jobs: job is in another batch");
+    if (j->nodes)
+      return fail(ctx, BP_ERR_UNSUPPORTED,
+                  "bp_batch_set_jobs: only per-view motion (motion_nodes = 0) is batched");
+    const int ch = j->pd.dtype == BP_F32 ? 4 : 8;  // elements per 16-byte staging chunk
+    if (j->pd.nu % ch)
+      return fail(ctx, BP_ERR_UNSUPPORTED,
+                  "bp_batch_set_jobs: detector width must be a multiple of 16 bytes");
+    if (!same_config(j, jobs[0]))
+      return fail(ctx, BP_ERR_INVALID_ARG,
+                  "bp_batch_set_jobs: members differ in dtype, weight, derivative, loss or "
+                  "optimiser");
+  }
+  for (bp_job* j : b->members) j->batch = nullptr;
+  b->members.assign(jobs, jobs + n_jobs);
+  for (bp_job* j : b->members) j->batch = b;
+  b->dirty = true;
+  return BP_OK;
+}
+
+int bp_batch_step(bp_batch* b, int n_iters, void* stream) {
+  if (!b || n_iters < 0) return BP_ERR_INVALID_ARG;
+  bp_ctx* ctx = b->ctx;
+  ctx->err.clear();
+  DeviceGuard g(b->device);
+  // cancelled members stop advancing from this step on
+  auto& m = b->members;
+  const size_t before = m.size();
+  for (bp_job* j : m)
+    if (j->cancelled) j->batch = nullptr;
+  m.erase(std::remove_if(m.begin(), m.end(), [](const bp_job* j) { return j->cancelled; }),
+          m.end());
+  if (m.size() != before) b->dirty = true;
+  if (n_iters == 0 || m.empty()) return BP_OK;
+  const bp_job* j0 = m[0];
+  const int fdk = j0->weight == BP_WEIGHT_FDK, exact = j0->deriv == BP_DERIV_BILINEAR_EXACT;
+  const int loss = j0->opt.loss == BP_LOSS_TV ? 1 : 0;
+  const int opt = j0->opt.optimizer == BP_OPT_ADAM ? 1 : 0;
+  cudaError_t e;
+  if (!b->exec || b->dtype != j0->pd.dtype || b->weight != j0->weight || b->deriv != j0->deriv ||
+      b->loss != loss || b->opt != opt) {
+    if (b->exec) {
+      // the graph of another configuration: wait for its queued replays
+      e = cudaEventSynchronize(b->last);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: wait");
+      cudaGraphExecDestroy(b->exec);
+      cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+    }
+    e = bpk::prepare_batch(j0->pd.dtype, fdk, exact);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: capture");
+    const cudaError_t le =
+        bpk::launch_batch_iteration(b->dev, j0->pd.dtype, fdk, exact, loss, opt, b->sms, b->cap);
+    e = cudaStreamEndCapture(b->cap, &b->graph);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+      if (b->graph) cudaGraphDestroy(b->graph);
+      b->graph = nullptr;
+      b->exec = nullptr;
+      return cuda_fail(ctx, e, "bp_batch_step: graph");
+    }
+    b->dtype = j0->pd.dtype;
+    b->weight = j0->weight;
+    b->deriv = j0->deriv;
+    b->loss = loss;
+    b->opt = opt;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (b->dirty) {
+    // the pinned table is rewritten only after its previous copy has run
+    e = cudaEventSynchronize(b->host_free[b->cur]);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: table");
+    fill_table(b, *b->host[b->cur]);
+    e = cudaMemcpyAsync(b->dev, b->host[b->cur], sizeof(bpk::BatchTable), cudaMemcpyHostToDevice,
+                        s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->host_free[b->cur], s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: table copy");
+    b->cur ^= 1;
+    b->dirty = false;
+  }
+  for (bp_job* j : m) {  // the members' set-up and earlier work come first
+    e = cudaStreamWaitEvent(s, j->done, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: wait");
+  }
+  for (int i = 0; i < n_iters; ++i) {
+    e = cudaGraphLaunch(b->exec, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: launch");
+  }
+  ctx->launches += (long long)bpk::BATCH_KERNELS * n_iters;
+  for (bp_job* j : m) {
+    j->queued += n_iters;
+    e = cudaEventRecord(j->done, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: record");
+  }
+  e = cudaEventRecord(b->last, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: record");
+  return BP_OK;
+}
+
+int bp_batch_size(const bp_batch* b) { return b ? (int)b->members.size() : -1; }
+
+void bp_batch_destroy(bp_batch* b) {
+  if (!b) return;
+  DeviceGuard g(b->device);
+  if (b->last) cudaEventSynchronize(b->last);
+  for (bp_job* j : b->members) j->batch = nullptr;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (int i = 0; i < 2; ++i) {
+    if (b->host_free[i]) {
+      cudaEventSynchronize(b->host_free[i]);
+      cudaEventDestroy(b->host_free[i]);
+    }
+    if (b->host[i]) cudaFreeHost(b->host[i]);
+  }
+  if (b->dev) cudaFree(b->dev);
+  if (b->last) cudaEventDestroy(b->last);
+  delete b;
 }
 
 }  // extern "C"

@@ -84,6 +84,23 @@ class MotionJob:
         N.check("bp_job_get_nodes", rc, self.ctx)
         return x
 
+    def cancel(self):
+        """Stop advancing the job (motion_step then raises BP_ERR_CANCELLED)."""
+        N.check("bp_job_cancel", N.lib().bp_job_cancel(self.handle), self.ctx)
+
+    def wait(self, timeout_ms=-1.0):
+        """Wait for the queued iterations; False if they still run after
+        timeout_ms (BP_ERR_TIMEOUT), True when done."""
+        rc = N.lib().bp_job_wait(self.handle, float(timeout_ms))
+        if rc == N.BP_ERR_TIMEOUT:
+            return False
+        N.check("bp_job_wait", rc, self.ctx)
+        return True
+
+    @property
+    def iterations_queued(self):
+        return int(N.lib().bp_job_iterations_queued(self.handle))
+
     def close(self):
         if getattr(self, "handle", None):
             N.lib().bp_job_destroy(self.handle)
@@ -100,3 +117,43 @@ def set_hbm_budget(nbytes, device=None):
     """Bytes that the live jobs of a device's context may hold (0 = free memory)."""
     ctx = N.context(device)
     N.check("bp_ctx_set_hbm_budget", N.lib().bp_ctx_set_hbm_budget(ctx, int(nbytes)), ctx)
+
+
+class Batch:
+    """Resident jobs advanced together (bp_batch_*): every stage of an
+    iteration is one persistent launch over the work items of all members."""
+
+    def __init__(self, max_jobs=8, device=None):
+        self.ctx = N.context(device)
+        h = ctypes.c_void_p()
+        N.check("bp_batch_create", N.lib().bp_batch_create(self.ctx, int(max_jobs), ctypes.byref(h)),
+                self.ctx)
+        self.handle = h
+        self.jobs = []
+
+    def set_jobs(self, jobs):
+        arr = (ctypes.c_void_p * max(1, len(jobs)))(*[j.handle.value for j in jobs])
+        N.check("bp_batch_set_jobs", N.lib().bp_batch_set_jobs(self.handle, arr, len(jobs)),
+                self.ctx)
+        self.jobs = list(jobs)
+
+    def step(self, n=1, stream=None):
+        """Queue n iterations of every member on `stream`."""
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        N.check("bp_batch_step", N.lib().bp_batch_step(self.handle, int(n), stream), self.ctx)
+
+    @property
+    def size(self):
+        return int(N.lib().bp_batch_size(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.lib().bp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -17,6 +17,8 @@ import torch
 from .build import LIB
 
 BP_OK = 0
+BP_ERR_TIMEOUT = -5
+BP_ERR_CANCELLED = -6
 STATUS = {0: "BP_OK", -1: "BP_ERR_INVALID_ARG", -2: "BP_ERR_OOM", -3: "BP_ERR_CUDA",
           -4: "BP_ERR_UNSUPPORTED", -5: "BP_ERR_TIMEOUT", -6: "BP_ERR_CANCELLED"}
 F32, F16, BF16 = 0, 1, 2
@@ -59,7 +61,15 @@ EXPORTS = ["bp_ctx_create", "bp_ctx_destroy", "bp_last_error", "bp_ctx_workspace
            "bp_gd_step", "bp_adam_step", "bp_job_create", "bp_job_bytes_for", "bp_job_bytes",
            "bp_ctx_set_hbm_budget", "motion_step", "bp_job_get_motion", "bp_job_volume",
            "bp_job_destroy", "bp_akima_motion", "bp_akima_motion_vjp", "bp_job_get_nodes",
-           "bp_fdk_filter"]
+           "bp_fdk_filter", "bp_job_cancel", "bp_job_wait", "bp_job_iterations_queued",
+           "bp_batch_create", "bp_batch_set_jobs", "bp_batch_step", "bp_batch_size",
+           "bp_batch_destroy", "bp_bounds_check", "bp_probe"]
+
+
+def library_path():
+    """The release library, or the one BP_GB300_LIB names (e.g. the
+    bounds-checking debug build)."""
+    return os.environ.get("BP_GB300_LIB") or LIB
 
 
 def lib():
@@ -68,11 +78,12 @@ def lib():
     if _lib is None:
         with _lock:
             if _lib is None:
-                if not os.path.exists(LIB):
+                path = library_path()
+                if not os.path.exists(path):
                     raise RuntimeError("bp_gb300 CUDA library not found at %s; build it with "
                                        "`python -m paper_2401_09283_gb300.build` or "
-                                       "__graft_entry__.build()" % LIB)
-                L = ctypes.CDLL(LIB)
+                                       "__graft_entry__.build()" % path)
+                L = ctypes.CDLL(path)
                 vp, dp, ip = c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int)
                 del dp, ip
                 L.bp_ctx_create.argtypes = [c_int, ctypes.POINTER(c_void_p)]
@@ -118,6 +129,18 @@ def lib():
                 L.bp_fdk_filter.argtypes = [vp, vp, c_int, c_int, c_int, c_double, c_double,
                                             c_double, c_double, c_int, vp, vp]
                 L.bp_akima_motion_vjp.argtypes = [vp, c_int, c_int, vp, vp, vp, vp]
+                L.bp_job_cancel.argtypes = [vp]
+                L.bp_job_wait.argtypes = [vp, c_double]
+                L.bp_job_iterations_queued.argtypes = [vp]
+                L.bp_batch_create.argtypes = [vp, c_int, ctypes.POINTER(c_void_p)]
+                L.bp_batch_set_jobs.argtypes = [vp, ctypes.POINTER(c_void_p), c_int]
+                L.bp_batch_step.argtypes = [vp, c_int, vp]
+                L.bp_batch_size.argtypes = [vp]
+                L.bp_batch_destroy.argtypes = [vp]
+                L.bp_batch_destroy.restype = None
+                L.bp_bounds_check.argtypes = [vp, c_int, ctypes.POINTER(ctypes.c_uint),
+                                              ctypes.POINTER(c_ll)]
+                L.bp_probe.argtypes = [vp, c_int, ctypes.POINTER(c_double), vp]
                 _lib = L
     return _lib
 
@@ -221,3 +244,11 @@ def kernel_times(device=None):
 
 def launch_count(device=None):
     return int(lib().bp_ctx_launch_count(context(device)))
+
+
+def probe(kind, device=None):
+    """bp_probe: a throughput measurement (per second) on the device."""
+    ctx = context(device)
+    out = c_double()
+    check("bp_probe", lib().bp_probe(ctx, int(kind), ctypes.byref(out), None), ctx)
+    return out.value
