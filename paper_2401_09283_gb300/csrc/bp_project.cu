@@ -1040,6 +1040,9 @@ __device__ __forceinline__ void vjp_view_central2(const T* buf, float* pout, int
   const f2 RU = pk2(t.ru[2], t.ru[2]), RV = pk2(t.rv[2], t.rv[2]), RW = pk2(t.rw[2], t.rw[2]);
   const f2 M2 = pk2(MAGIC, MAGIC), TWO = pk2(2.0f, 2.0f), HALF = pk2(0.5f, 0.5f);
   const f2 WG = pk2(t.wgt, t.wgt);
+  const f2 WGD = pk2(t.wgtd, t.wgtd);
+  // pixel index offset of the floor bits: (av - MAGIC_BITS) nu + au - MAGIC_BITS
+  const unsigned pofs = (unsigned)(t.av - MAGIC_BITS) * (unsigned)nu + (unsigned)(t.au - MAGIC_BITS);
   const f2 zero = pk2(0.0f, 0.0f);
   f2 dz = pk2(-0.5f * (ZB - 1), 1.0f - 0.5f * (ZB - 1));
   f2 ndz = pk2(0.5f * (ZB - 1), 0.5f * (ZB - 1) - 1.0f);
@@ -1084,22 +1087,33 @@ __device__ __forceinline__ void vjp_view_central2(const T* buf, float* pout, int
     Z0 = fma2(A0, dz, Z0);
     Z1 = fma2(A1, dz, Z1);
     Z2 = fma2(NA2, ndz, Z2);
-    if (PROJ) {  // fused data VJP, per voxel: same sample, dequantised weight
-      float rl, rh, tul, tuh, tvl, tvh;
-      up2(r, rl, rh);
-      up2(tu, tul, tuh);
-      up2(tv, tvl, tvh);
+    if (PROJ) {
+      // fused data VJP, per voxel: the same sample's bilinear weights (the
+      // scalar scatter's formulas, packed), dequantised view weight, four
+      // FP32 atomic adds per voxel; interior tiles only (no bounds checks)
+      const f2 SD = mul2(D, FDK ? mul2(r, mul2(r, WGD)) : WGD);
+      const f2 Q1 = mul2(SD, tv), Q0 = sub2(SD, Q1);
+      const f2 W11 = mul2(Q1, tu), W01 = sub2(Q1, W11), W10 = mul2(Q0, tu), W00 = sub2(Q0, W10);
+      float w[4][2];
+      up2(W00, w[0][0], w[0][1]);
+      up2(W10, w[1][0], w[1][1]);
+      up2(W01, w[2][0], w[2][1]);
+      up2(W11, w[3][0], w[3][1]);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int k = 2 * p + h;
-        if (delta[k] == 0.0f) continue;
-        Sample s;
-        const float rk = h ? rh : rl;
-        s.tu = h ? tuh : tul;
-        s.tv = h ? tvh : tvl;
-        s.iu = __float_as_int(h ? bxh : bxl) - MAGIC_BITS + t.au;
-        s.iv = __float_as_int(h ? byh : byl) - MAGIC_BITS + t.av;
-        scatter_sample<EDGE>(pout, nu, nv, s, delta[k] * (FDK ? rk * (rk * t.wgtd) : t.wgtd));
+        int bxi = __float_as_int(h ? bxh : bxl), byi = __float_as_int(h ? byh : byl);
+#ifdef BP_BOUNDS_CHECK
+        int iu = bxi - MAGIC_BITS + t.au, iv = byi - MAGIC_BITS + t.av;
+        bc_interior(BC_SCATTER, iu, iv, nu, nv);
+        bxi = iu + MAGIC_BITS - t.au;
+        byi = iv + MAGIC_BITS - t.av;
+#endif
+        // (iv * nu + iu) from the floor bits, in 32-bit wraparound arithmetic
+        float* q = pout + ((unsigned)byi * (unsigned)nu + (unsigned)bxi + pofs);
+        atomicAdd(q, w[0][h]);
+        atomicAdd(q + 1, w[1][h]);
+        atomicAdd(q + nu, w[2][h]);
+        atomicAdd(q + nu + 1, w[3][h]);
       }
     }
   }
@@ -1115,6 +1129,9 @@ __device__ __forceinline__ void vjp_view_central2(const T* buf, float* pout, int
 // Fused data VJP by lines (below) or per sample (the scalar loop).
 #ifndef BP_VJP_LINES
 #define BP_VJP_LINES 1
+#endif
+#ifndef BP_VJP_LINE_DU
+#define BP_VJP_LINE_DU 0.6f
 #endif
 
 // Data VJP of one staged central-safe (hence interior) tile-view, by lines:
@@ -1220,12 +1237,21 @@ __device__ __forceinline__ void vjp_tile_view(const T* img, const float2* gimg, 
                                               const float (&delta)[ZB], const float* dsm,
                                               float (*redv)[12]) {
   float S[3] = {0.0f, 0.0f, 0.0f}, Z[3] = {0.0f, 0.0f, 0.0f};
-  if (staged && !EXACT && (!PROJ || BP_VJP_LINES)) {
+  if (staged && !EXACT) {
     // CENTRAL footprints are staged only for central-safe, hence interior,
-    // tiles
-    vjp_view_central2<ZB, E, FDK, false, false, P>(buf, pout, pi.nu, pi.nv, t, ti.dx, ti.dy, delta,
-                                                   S, Z);
-    if (PROJ) proj_lines<ZB, FDK>(pout, pi.nu, t, dsm);
+    // tiles.  With the fused data VJP: the line pass where samples along
+    // the ray-parallel axis move by at most BP_VJP_LINE_DU px per voxel
+    // (there it merges most: about 2 du + 0.25 atomics per sample), else
+    // four atomics per sample from the packed loop, far fewer instructions
+    if (PROJ && BP_VJP_LINES &&
+        fminf(fabsf(t.ru[0]), fabsf(t.ru[1])) <= BP_VJP_LINE_DU * t.W0) {
+      vjp_view_central2<ZB, E, FDK, false, false, P>(buf, pout, pi.nu, pi.nv, t, ti.dx, ti.dy,
+                                                     delta, S, Z);
+      proj_lines<ZB, FDK>(pout, pi.nu, t, dsm);
+    } else {
+      vjp_view_central2<ZB, E, FDK, false, PROJ, P>(buf, pout, pi.nu, pi.nv, t, ti.dx, ti.dy,
+                                                    delta, S, Z);
+    }
   } else if (staged) {
     if (t.mode == MODE_INTERIOR || !PROJ)
       vjp_view<ZB, T, FDK, EXACT, false, PROJ, SRC_SMEM, E, P>(img, gimg, buf, pout, pi.rs, pi.nu,
