@@ -354,16 +354,18 @@ int bp_job_iterations_queued(const bp_job* job);
  * (Eqs. 4-5), FP64 reduction and chain (Eq. 2), update -- is ONE persistent
  * launch whose blocks walk the work items (views, tiles, (tile, view chunk)
  * pairs, loss chunks) of every member, so jobs of different volume and view
- * counts share each kernel and fill the GPU together.  The kernels read the
- * member set from a device table; one CUDA graph, captured at the first step,
- * serves every later member set.  Every item runs the per-job arithmetic:
- * a member's iterations are bit for bit those of motion_step.
+ * counts share each kernel and fill the GPU together.  The member table is a
+ * kernel parameter; each member set gets one captured CUDA graph of the
+ * iteration (made at the first step after the set changes; the graph of an
+ * earlier set is freed once its queued replays have run).  Every item runs
+ * the per-job arithmetic: a member's iterations are bit for bit those of
+ * motion_step.
  * Members must share dtype, weight, derivative mode, loss and optimiser,
  * use per-view motion (motion_nodes = 0) and have detector rows of a
  * multiple of 16 bytes; a job is a member of at most one batch and is not
  * advanced by motion_step while it is one.  The paper has no counterpart. */
 typedef struct bp_batch bp_batch;
-/* max_jobs: 1..64 members. */
+/* max_jobs: 1..32 members. */
 int bp_batch_create(bp_ctx* ctx, int max_jobs, bp_batch** out);
 /* Replace the member set (n_jobs = 0 empties it); takes effect at the next
  * step.  BP_ERR_INVALID_ARG / BP_ERR_UNSUPPORTED / BP_ERR_CANCELLED for a

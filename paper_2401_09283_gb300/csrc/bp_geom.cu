@@ -557,31 +557,28 @@ cudaError_t launch_tv(const float* vol, int nx, int ny, int nz, float eps, doubl
 
 // ------------------------------------------------------------------- batches
 // The per-job kernels above, as launches over the work items of every member
-// of a batch table (grid-stride loops, so any grid size covers any member
-// set).  Each item runs exactly the per-job arithmetic: a job gives bit for
-// bit the same iteration in a batch as alone.
+// of a batch table (a __grid_constant__ parameter; grid-stride loops, so any
+// grid size covers any member set).  Each item runs exactly the per-job
+// arithmetic: a job gives bit for bit the same iteration in a batch as alone.
 
-__global__ void batch_compose_kernel(BatchTable* __restrict__ t, int fdk) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {  // the work counters of this iteration
-    t->next_fwd = 0u;
-    t->next_vjp = 0u;
-  }
-  const int n = t->njobs, total = t->off_view[n];
+__global__ void batch_compose_kernel(const __grid_constant__ BatchTable t, int fdk,
+                                     unsigned* counter) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0u;  // the forward's work counter
+  const int n = t.njobs, total = t.off_view[n];
   for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
-    const int j = batch_find(t->off_view, n, w);
-    const BatchJob& J = t->job[j];
-    compose_view(J.P, J.theta, J.vw, J.scale, fdk, J.sid, J.vi, J.geom, nullptr,
-                 w - t->off_view[j]);
+    const int j = batch_find(t.off_view, n, w);
+    const BatchJob& J = t.job[j];
+    compose_view(J.P, J.theta, J.vw, J.scale, fdk, J.sid, J.vi, J.geom, nullptr, w - t.off_view[j]);
   }
 }
 
 template <int LOSS>
-__global__ void batch_loss_kernel(const BatchTable* __restrict__ t) {
-  const int n = t->njobs, total = t->off_loss[n];
+__global__ void batch_loss_kernel(const __grid_constant__ BatchTable t) {
+  const int n = t.njobs, total = t.off_loss[n];
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
-    const int j = batch_find(t->off_loss, n, w);
-    const BatchJob& J = t->job[j];
-    const int b = w - t->off_loss[j];
+    const int j = batch_find(t.off_loss, n, w);
+    const BatchJob& J = t.job[j];
+    const int b = w - t.off_loss[j];
     if (LOSS == 1)
       tv_block(J.vol, J.vi.nx, J.vi.ny, J.vi.nz, J.tv_eps, J.blk, J.dvol, b, J.nblk);
     else
@@ -591,30 +588,30 @@ __global__ void batch_loss_kernel(const BatchTable* __restrict__ t) {
 }
 
 template <int LOSS>
-__global__ void batch_loss_finish_kernel(const BatchTable* __restrict__ t) {
-  for (int j = blockIdx.x; j < t->njobs; j += gridDim.x) {
-    const BatchJob& J = t->job[j];
+__global__ void batch_loss_finish_kernel(const __grid_constant__ BatchTable t) {
+  for (int j = blockIdx.x; j < t.njobs; j += gridDim.x) {
+    const BatchJob& J = t.job[j];
     const double K = (double)J.vi.nx * J.vi.ny * J.vi.nz;
     loss_finish_hist(J.blk, J.nblk, K, LOSS == 1 ? 1.0 : -1.0, J.hist, J.iter, J.max_iters);
     __syncthreads();
   }
 }
 
-__global__ void batch_reduce_kernel(const BatchTable* __restrict__ t) {
-  const int n = t->njobs, total = t->off_view[n];
+__global__ void batch_reduce_kernel(const __grid_constant__ BatchTable t) {
+  const int n = t.njobs, total = t.off_view[n];
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
-    const int j = batch_find(t->off_view, n, w);
-    const BatchJob& J = t->job[j];
+    const int j = batch_find(t.off_view, n, w);
+    const BatchJob& J = t.job[j];
     reduce_chain_view(J.partials, J.ntiles_v, J.vi, J.P, J.theta, nullptr, J.gth,
-                      w - t->off_view[j]);
+                      w - t.off_view[j]);
     __syncthreads();
   }
 }
 
 template <int OPT>
-__global__ void batch_opt_kernel(const BatchTable* __restrict__ t) {
-  for (int j = blockIdx.x; j < t->njobs; j += gridDim.x) {
-    const BatchJob& J = t->job[j];
+__global__ void batch_opt_kernel(const __grid_constant__ BatchTable t) {
+  for (int j = blockIdx.x; j < t.njobs; j += gridDim.x) {
+    const BatchJob& J = t.job[j];
     if (OPT == 1)
       adam_dev_body(J.V, J.theta, J.gth, J.m1, J.m2, J.lr_t, J.lr_r, J.beta1, J.beta2, J.eps,
                     J.iter, J.gauge);
@@ -624,29 +621,30 @@ __global__ void batch_opt_kernel(const BatchTable* __restrict__ t) {
   }
 }
 
-cudaError_t launch_batch_iteration(BatchTable* tab, int dtype, int fdk, int exact, int loss,
-                                   int opt, int sms, cudaStream_t s) {
-  batch_compose_kernel<<<sms, 128, 0, s>>>(tab, fdk);
+cudaError_t launch_batch_iteration(const BatchTable& tab, unsigned* counter, int dtype, int fdk,
+                                   int exact, int loss, int opt, int sms, cudaStream_t s) {
+  batch_compose_kernel<<<sms, 128, 0, s>>>(tab, fdk, counter);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_batch_forward(tab, dtype, fdk, sms, s);
+  e = launch_batch_forward(tab, counter, dtype, fdk, sms, s);
   if (e != cudaSuccess) return e;
+  const int jb = tab.njobs > 0 ? tab.njobs : 1;
   if (loss == 1) {
     batch_loss_kernel<1><<<sms * 8, SH_THREADS, 0, s>>>(tab);
-    batch_loss_finish_kernel<1><<<BATCH_MAX_JOBS, SH_THREADS, 0, s>>>(tab);
+    batch_loss_finish_kernel<1><<<jb, SH_THREADS, 0, s>>>(tab);
   } else {
     batch_loss_kernel<0><<<sms * 8, SH_THREADS, 0, s>>>(tab);
-    batch_loss_finish_kernel<0><<<BATCH_MAX_JOBS, SH_THREADS, 0, s>>>(tab);
+    batch_loss_finish_kernel<0><<<jb, SH_THREADS, 0, s>>>(tab);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_batch_vjp(tab, dtype, fdk, exact, sms, s);
+  e = launch_batch_vjp(tab, dtype, fdk, exact, s);
   if (e != cudaSuccess) return e;
   batch_reduce_kernel<<<sms * 8, 256, 0, s>>>(tab);
   if (opt == 1)
-    batch_opt_kernel<1><<<BATCH_MAX_JOBS, 256, 0, s>>>(tab);
+    batch_opt_kernel<1><<<jb, 256, 0, s>>>(tab);
   else
-    batch_opt_kernel<0><<<BATCH_MAX_JOBS, 256, 0, s>>>(tab);
+    batch_opt_kernel<0><<<jb, 256, 0, s>>>(tab);
   return cudaGetLastError();
 }
 

@@ -159,11 +159,15 @@ cudaError_t launch_fdk_filter(const float* raw, int V, int nv, int nu, int ext, 
 // ---------------------------------------------------------------- batches
 // Several motion-estimation jobs advanced together: each stage of an
 // iteration is one launch over the work items of every member job (views,
-// tiles, (tile, view chunk) pairs, loss chunks).  The kernels read the member
-// set from a device table, so one captured graph serves any set of up to
-// BATCH_MAX_JOBS members.  Members share dtype, weight, derivative mode, loss
-// and optimiser (template or launch-uniform parameters).
-constexpr int BATCH_MAX_JOBS = 64;
+// tiles, (tile, view chunk) pairs, loss chunks).  The member table is a
+// __grid_constant__ kernel parameter: the kernels read each job's sizes and
+// pointers from read-only parameter space, as the per-job kernels read their
+// arguments (from a table in shared or global memory the compiler must
+// assume aliased, the VJP ran 26 % more instructions).  Members share dtype,
+// weight, derivative mode, loss and optimiser (template or launch-uniform
+// parameters).  At most BATCH_MAX_JOBS members (the table fits the 32 KB of
+// kernel parameters).
+constexpr int BATCH_MAX_JOBS = 32;
 
 struct BatchJob {
   const void* proj;        // [V][nv][nu] compact, the batch's dtype
@@ -188,11 +192,6 @@ struct BatchJob {
 };
 
 struct BatchTable {
-  // work counters of the two persistent stages (forward, VJP): CTAs take
-  // their next item with an atomic add, so items run in order and a CTA
-  // that drew cheap items takes more; reset by the first kernel of an
-  // iteration
-  unsigned int next_fwd, next_vjp;
   int njobs;
   int off_view[BATCH_MAX_JOBS + 1];  // prefix sums of V (compose, reduction)
   int off_fwd[BATCH_MAX_JOBS + 1];   // of forward tiles
@@ -200,6 +199,7 @@ struct BatchTable {
   int off_vjp[BATCH_MAX_JOBS + 1];   // of VJP (tile, view chunk) items
   BatchJob job[BATCH_MAX_JOBS];
 };
+static_assert(sizeof(BatchTable) <= 30000, "the member table must fit the kernel parameters");
 
 // Index of the job whose range [off[j], off[j+1]) holds work item w.
 __host__ __device__ inline int batch_find(const int* off, int n, int w) {
@@ -217,16 +217,17 @@ int forward_zb();
 int vjp_view_chunk(const ProjInfo& pi, int dtype, int exact);
 
 // One iteration of every member: compose -> forward -> loss -> VJP ->
-// reduction and chain -> update, as persistent launches over the table's
-// work items (grids sized by the SM count, not by the members).
+// reduction and chain -> update, one launch per stage over the table's work
+// items: the forward persistent (SMs x 4 CTAs taking tiles from *counter,
+// which the compose launch resets), the VJP grouped (one block per (tile,
+// view chunk) item), the small stages grid-stride loops.
 // loss: 0 sharpness, 1 TV; opt: 0 Eq. 6 step, 1 Adam.
 cudaError_t prepare_batch(int dtype, int fdk, int exact);
-// The two persistent stages (bp_project.cu): SMs x resident CTAs blocks.
-cudaError_t launch_batch_forward(BatchTable* tab, int dtype, int fdk, int sms, cudaStream_t s);
-cudaError_t launch_batch_vjp(BatchTable* tab, int dtype, int fdk, int exact, int sms,
-                             cudaStream_t s);
-cudaError_t launch_batch_iteration(BatchTable* tab, int dtype, int fdk, int exact, int loss,
-                                   int opt, int sms, cudaStream_t s);
+cudaError_t launch_batch_iteration(const BatchTable& tab, unsigned* counter, int dtype, int fdk,
+                                   int exact, int loss, int opt, int sms, cudaStream_t s);
+cudaError_t launch_batch_forward(const BatchTable& tab, unsigned* counter, int dtype, int fdk,
+                                 int sms, cudaStream_t s);
+cudaError_t launch_batch_vjp(const BatchTable& tab, int dtype, int fdk, int exact, cudaStream_t s);
 constexpr int BATCH_KERNELS = 7;  // launches per batched iteration
 
 // Bounds-check word of debug builds (-DBP_BOUNDS_CHECK): op 0 reads the flag

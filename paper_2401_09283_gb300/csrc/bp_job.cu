@@ -46,17 +46,19 @@ struct bp_batch {
   bp_ctx* ctx = nullptr;
   int device = 0, sms = 0, max_jobs = 0;
   std::vector<bp_job*> members;
-  // member configuration the captured graph was made for
-  int dtype = -1, weight = -1, deriv = -1, loss = -1, opt = -1;
-  bpk::BatchTable* host[2] = {nullptr, nullptr};  // pinned, alternating
-  cudaEvent_t host_free[2] = {nullptr, nullptr};  // copy out of host[i] done
-  int cur = 0;
-  bool dirty = true;
-  bpk::BatchTable* dev = nullptr;
+  bool dirty = true;                // the member set changed since the graph was made
+  bpk::BatchTable table{};          // the graph's member table (a kernel parameter)
+  unsigned* counter = nullptr;      // the persistent forward's work counter (device)
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaEvent_t last = nullptr;  // after the latest queued step
+  cudaEvent_t last = nullptr;       // after the latest queued step
+  struct Retired {                  // graphs of earlier member sets, freed once idle
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    cudaEvent_t done;
+  };
+  std::vector<Retired> retired;
 };
 
 namespace {
@@ -548,11 +550,8 @@ int bp_batch_create(bp_ctx* ctx, int max_jobs, bp_batch** out) {
   b->device = ctx->device;
   b->max_jobs = max_jobs;
   cudaError_t e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-    e = cudaMallocHost((void**)&b->host[i], sizeof(bpk::BatchTable));
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->host_free[i], cudaEventDisableTiming);
-  }
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->dev, sizeof(bpk::BatchTable));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->counter, 256);
+  if (e == cudaSuccess) e = cudaMemset(b->counter, 0, 256);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->last, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -591,12 +590,35 @@ int bp_batch_set_jobs(bp_batch* b, bp_job* const* jobs, int n_jobs) {
                   "bp_batch_set_jobs: members differ in dtype, weight, derivative, loss or "
                   "optimiser");
   }
+  std::vector<bp_job*> next(jobs, jobs + n_jobs);
+  if (next != b->members) b->dirty = true;
   for (bp_job* j : b->members) j->batch = nullptr;
-  b->members.assign(jobs, jobs + n_jobs);
+  b->members = next;
   for (bp_job* j : b->members) j->batch = b;
-  b->dirty = true;
   return BP_OK;
 }
+
+namespace {
+
+// Free the graphs of earlier member sets whose replays have finished (all,
+// waiting for them, when wait is set).
+void free_retired(bp_batch* b, bool wait) {
+  auto& r = b->retired;
+  for (size_t k = 0; k < r.size();) {
+    if (wait) cudaEventSynchronize(r[k].done);
+    if (cudaEventQuery(r[k].done) == cudaSuccess) {
+      cudaGraphExecDestroy(r[k].exec);
+      cudaGraphDestroy(r[k].graph);
+      cudaEventDestroy(r[k].done);
+      r.erase(r.begin() + (long)k);
+    } else {
+      cudaGetLastError();
+      ++k;
+    }
+  }
+}
+
+}  // namespace
 
 int bp_batch_step(bp_batch* b, int n_iters, void* stream) {
   if (!b || n_iters < 0) return BP_ERR_INVALID_ARG;
@@ -611,28 +633,31 @@ int bp_batch_step(bp_batch* b, int n_iters, void* stream) {
   m.erase(std::remove_if(m.begin(), m.end(), [](const bp_job* j) { return j->cancelled; }),
           m.end());
   if (m.size() != before) b->dirty = true;
+  free_retired(b, false);
   if (n_iters == 0 || m.empty()) return BP_OK;
   const bp_job* j0 = m[0];
   const int fdk = j0->weight == BP_WEIGHT_FDK, exact = j0->deriv == BP_DERIV_BILINEAR_EXACT;
   const int loss = j0->opt.loss == BP_LOSS_TV ? 1 : 0;
   const int opt = j0->opt.optimizer == BP_OPT_ADAM ? 1 : 0;
   cudaError_t e;
-  if (!b->exec || b->dtype != j0->pd.dtype || b->weight != j0->weight || b->deriv != j0->deriv ||
-      b->loss != loss || b->opt != opt) {
+  if (b->dirty || !b->exec) {
+    // a new member set: one graph of the iteration with this member table
+    // (the earlier graph is freed once its queued replays have run)
     if (b->exec) {
-      // the graph of another configuration: wait for its queued replays
-      e = cudaEventSynchronize(b->last);
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: wait");
-      cudaGraphExecDestroy(b->exec);
-      cudaGraphDestroy(b->graph);
-      b->exec = nullptr;
+      cudaEvent_t fresh = nullptr;
+      e = cudaEventCreateWithFlags(&fresh, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: event");
+      b->retired.push_back({b->graph, b->exec, b->last});
+      b->last = fresh;
       b->graph = nullptr;
+      b->exec = nullptr;
     }
+    fill_table(b, b->table);
     e = bpk::prepare_batch(j0->pd.dtype, fdk, exact);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: capture");
-    const cudaError_t le =
-        bpk::launch_batch_iteration(b->dev, j0->pd.dtype, fdk, exact, loss, opt, b->sms, b->cap);
+    const cudaError_t le = bpk::launch_batch_iteration(b->table, b->counter, j0->pd.dtype, fdk,
+                                                       exact, loss, opt, b->sms, b->cap);
     e = cudaStreamEndCapture(b->cap, &b->graph);
     if (le != cudaSuccess) e = le;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
@@ -642,25 +667,9 @@ int bp_batch_step(bp_batch* b, int n_iters, void* stream) {
       b->exec = nullptr;
       return cuda_fail(ctx, e, "bp_batch_step: graph");
     }
-    b->dtype = j0->pd.dtype;
-    b->weight = j0->weight;
-    b->deriv = j0->deriv;
-    b->loss = loss;
-    b->opt = opt;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  if (b->dirty) {
-    // the pinned table is rewritten only after its previous copy has run
-    e = cudaEventSynchronize(b->host_free[b->cur]);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: table");
-    fill_table(b, *b->host[b->cur]);
-    e = cudaMemcpyAsync(b->dev, b->host[b->cur], sizeof(bpk::BatchTable), cudaMemcpyHostToDevice,
-                        s);
-    if (e == cudaSuccess) e = cudaEventRecord(b->host_free[b->cur], s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: table copy");
-    b->cur ^= 1;
     b->dirty = false;
   }
+  cudaStream_t s = (cudaStream_t)stream;
   for (bp_job* j : m) {  // the members' set-up and earlier work come first
     e = cudaStreamWaitEvent(s, j->done, 0);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: wait");
@@ -686,18 +695,12 @@ void bp_batch_destroy(bp_batch* b) {
   if (!b) return;
   DeviceGuard g(b->device);
   if (b->last) cudaEventSynchronize(b->last);
+  free_retired(b, true);
   for (bp_job* j : b->members) j->batch = nullptr;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
-  for (int i = 0; i < 2; ++i) {
-    if (b->host_free[i]) {
-      cudaEventSynchronize(b->host_free[i]);
-      cudaEventDestroy(b->host_free[i]);
-    }
-    if (b->host[i]) cudaFreeHost(b->host[i]);
-  }
-  if (b->dev) cudaFree(b->dev);
+  if (b->counter) cudaFree(b->counter);
   if (b->last) cudaEventDestroy(b->last);
   delete b;
 }

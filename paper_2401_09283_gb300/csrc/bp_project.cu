@@ -1131,21 +1131,21 @@ __device__ __forceinline__ void vjp_view_central2(const T* buf, float* pout, int
 #define BP_VJP_LINES 1
 #endif
 #ifndef BP_VJP_LINE_DU
-#define BP_VJP_LINE_DU 0.6f
+#define BP_VJP_LINE_DU 0.5f
 #endif
 
 // Data VJP of one staged central-safe (hence interior) tile-view, by lines:
 // thread (a, b) walks the 16 voxels of the tile's line along the axis, x or
-// y, whose voxels project closest together on the detector (per voxel the
-// sample moves by at most ~1.9 px along u there and barely along v), in the
-// direction of increasing u.  The bilinear weights of consecutive samples in
-// the same detector row pair (iv, iv+1) and the same or the next column are
-// merged in a 2 x 2 register window (rows r, r+1; columns c, c+1), and a
-// column is added to dL/dproj (FP32 L2 atomics) only when the window moves
-// past it, instead of four atomics per sample.  On the c2 geometry that is
-// 2.2 atomic adds per sample (measured by simulating the window over the
-// views).  Exact to rounding: the same weights, summed in another order.
-// dsm holds the tile's dL/dvol as [z][y][x] with a row pitch of TX + 1.
+// y, whose voxels project closest together on the detector (there the sample
+// moves by less than the per-view threshold along u per voxel and barely
+// along v), in the direction of increasing u.  The bilinear weights of
+// consecutive samples that fall in the same detector cell (same floor pixel)
+// are summed in registers, and a cell's four pixels are added to dL/dproj
+// (FP32 L2 atomics) only when the line leaves it: about 4 (du + 1/16) atomic
+// adds per sample instead of 4.  The arithmetic runs on packed pairs of
+// consecutive voxels (f32x2), as in the motion loop.  Exact to rounding: the
+// same weights, summed in another order.  dsm holds the tile's dL/dvol as
+// [z][y][x] with a row pitch of TX + 1.
 template <int ZB, bool FDK>
 __device__ __forceinline__ void proj_lines(float* __restrict__ pout, int nu, const TileView& t,
                                            const float* __restrict__ dsm) {
@@ -1156,73 +1156,82 @@ __device__ __forceinline__ void proj_lines(float* __restrict__ pout, int nu, con
   // x-lines: voxels (k, a, b); y-lines: (a, k, b)
   const float ou = alongx ? t.ru[1] : t.ru[0], ov = alongx ? t.rv[1] : t.rv[0];
   const float ow = alongx ? t.rw[1] : t.rw[0];
-  const float su = alongx ? t.ru[0] : t.ru[1], sv = alongx ? t.rv[0] : t.rv[1];
-  const float sw = alongx ? t.rw[0] : t.rw[1];
+  float su = alongx ? t.ru[0] : t.ru[1], sv = alongx ? t.rv[0] : t.rv[1];
+  float sw = alongx ? t.rw[0] : t.rw[1];
   const float u0 = fmaf(fb, t.ru[2], fmaf(fa, ou, t.U0));
   const float v0 = fmaf(fb, t.rv[2], fmaf(fa, ov, t.V0));
   const float w0 = fmaf(fb, t.rw[2], fmaf(fa, ow, t.W0));
+  // walk in the direction of increasing u: step kk visits voxel k = 15 - kk
+  // when the axis runs against u (the negated steps give the same positions)
   const bool rev = su < 0.0f;
+  if (rev) {
+    su = -su;
+    sv = -sv;
+    sw = -sw;
+  }
   const float* dl = alongx ? dsm + (b * TY + a) * (TX + 1) : dsm + b * TY * (TX + 1) + a;
   const int dstep = alongx ? 1 : TX + 1;
-  int r = 0, c = 0;
+  const f2 U0 = pk2(u0, u0), V0 = pk2(v0, v0), W0 = pk2(w0, w0);
+  const f2 SU = pk2(su, su), SV = pk2(sv, sv), SW = pk2(sw, sw);
+  const f2 M2 = pk2(MAGIC, MAGIC), TWO = pk2(2.0f, 2.0f), WGD = pk2(t.wgtd, t.wgtd);
+  const unsigned pofs = (unsigned)(t.av - MAGIC_BITS) * (unsigned)nu + (unsigned)(t.au - MAGIC_BITS);
+  int cb = 0, rb = 0;  // the open cell, as floor bits
   bool have = false;
   float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
-#pragma unroll 4
-  for (int kk = 0; kk < TX; ++kk) {
-    const int k = rev ? TX - 1 - kk : kk;
-    const float dk = k - 0.5f * (TX - 1);
-    const float u = fmaf(dk, su, u0), v = fmaf(dk, sv, v0), w = fmaf(dk, sw, w0);
-    const float rw = rcp_approx(w);
-    const float x = u * rw, y = v * rw;
-    const float rx = __fadd_rd(x, MAGIC), ry = __fadd_rd(y, MAGIC);
-    const float tu = x - (rx - MAGIC), tv = y - (ry - MAGIC);
-    int iu = __float_as_int(rx) - MAGIC_BITS + t.au, iv = __float_as_int(ry) - MAGIC_BITS + t.av;
-    const float sd = dl[k * dstep] * (FDK ? rw * (rw * t.wgtd) : t.wgtd);
-    const float q1 = sd * tv, q0 = sd - q1;
-    const float w11 = q1 * tu, w01 = q1 - w11, w10 = q0 * tu, w00 = q0 - w10;
-    const bool same = have && iv == r;
-    const bool keep = same && iu == c, slide = same && iu == c + 1;
-    if (have && !keep) {  // columns the window leaves
-      int fc = c, fr = r;
-      bc_interior(BC_SCATTER, fc, fr, nu, 1 << 30);
-      float* p = pout + (long long)fr * nu + fc;
-      if (a0 != 0.0f) atomicAdd(p, a0);
-      if (b0 != 0.0f) atomicAdd(p + nu, b0);
-      if (!slide) {
-        if (a1 != 0.0f) atomicAdd(p + 1, a1);
-        if (b1 != 0.0f) atomicAdd(p + nu + 1, b1);
+  f2 dk = pk2(-0.5f * (TX - 1), 1.0f - 0.5f * (TX - 1));
+#pragma unroll 2
+  for (int p = 0; p < TX / 2; ++p) {
+    if (p) dk = add2(dk, TWO);
+    const f2 u = fma2(dk, SU, U0), v = fma2(dk, SV, V0), w = fma2(dk, SW, W0);
+    float wl, wh;
+    up2(w, wl, wh);
+    const f2 r = pk2(rcp_approx(wl), rcp_approx(wh));
+    const f2 x = mul2(u, r), y = mul2(v, r);
+    const f2 rx = add2_rd(x, M2), ry = add2_rd(y, M2);
+    const f2 tu = sub2(x, sub2(rx, M2)), tv = sub2(y, sub2(ry, M2));
+    const int k0 = rev ? TX - 1 - 2 * p : 2 * p, k1 = rev ? k0 - 1 : k0 + 1;
+    const f2 D = pk2(dl[k0 * dstep], dl[k1 * dstep]);
+    const f2 SD = mul2(D, FDK ? mul2(r, mul2(r, WGD)) : WGD);
+    const f2 Q1 = mul2(SD, tv), Q0 = sub2(SD, Q1);
+    const f2 W11 = mul2(Q1, tu), W01 = sub2(Q1, W11), W10 = mul2(Q0, tu), W00 = sub2(Q0, W10);
+    float bxf[2], byf[2], ww[4][2];
+    up2(rx, bxf[0], bxf[1]);
+    up2(ry, byf[0], byf[1]);
+    up2(W00, ww[0][0], ww[0][1]);
+    up2(W10, ww[1][0], ww[1][1]);
+    up2(W01, ww[2][0], ww[2][1]);
+    up2(W11, ww[3][0], ww[3][1]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int bx = __float_as_int(bxf[h]), by = __float_as_int(byf[h]);
+      const bool keep = have && bx == cb && by == rb;
+      if (have && !keep) {  // the line leaves the open cell: add its four pixels
+        int fc = cb - MAGIC_BITS + t.au, fr = rb - MAGIC_BITS + t.av;
+        bc_interior(BC_SCATTER, fc, fr, nu, 1 << 30);
+        float* q = pout + ((unsigned)(fr + MAGIC_BITS - t.av) * (unsigned)nu +
+                           (unsigned)(fc + MAGIC_BITS - t.au) + pofs);
+        atomicAdd(q, a0);
+        atomicAdd(q + 1, a1);
+        atomicAdd(q + nu, b0);
+        atomicAdd(q + nu + 1, b1);
       }
-    }
-    if (keep) {
-      a0 += w00;
-      a1 += w10;
-      b0 += w01;
-      b1 += w11;
-    } else if (slide) {
-      a0 = a1 + w00;
-      a1 = w10;
-      b0 = b1 + w01;
-      b1 = w11;
-      c = iu;
-    } else {
-      a0 = w00;
-      a1 = w10;
-      b0 = w01;
-      b1 = w11;
-      c = iu;
-      r = iv;
+      a0 = (keep ? a0 : 0.0f) + ww[0][h];
+      a1 = (keep ? a1 : 0.0f) + ww[1][h];
+      b0 = (keep ? b0 : 0.0f) + ww[2][h];
+      b1 = (keep ? b1 : 0.0f) + ww[3][h];
+      cb = bx;
+      rb = by;
       have = true;
     }
   }
-  if (have) {
-    int fc = c, fr = r;
-    bc_interior(BC_SCATTER, fc, fr, nu, 1 << 30);
-    float* p = pout + (long long)fr * nu + fc;
-    if (a0 != 0.0f) atomicAdd(p, a0);
-    if (a1 != 0.0f) atomicAdd(p + 1, a1);
-    if (b0 != 0.0f) atomicAdd(p + nu, b0);
-    if (b1 != 0.0f) atomicAdd(p + nu + 1, b1);
-  }
+  int fc = cb - MAGIC_BITS + t.au, fr = rb - MAGIC_BITS + t.av;
+  bc_interior(BC_SCATTER, fc, fr, nu, 1 << 30);
+  float* q = pout + ((unsigned)(fr + MAGIC_BITS - t.av) * (unsigned)nu +
+                     (unsigned)(fc + MAGIC_BITS - t.au) + pofs);
+  atomicAdd(q, a0);
+  atomicAdd(q + 1, a1);
+  atomicAdd(q + nu, b0);
+  atomicAdd(q + nu + 1, b1);
 }
 
 // One view of one tile: the sample loop (from the staged footprint when it
@@ -1241,8 +1250,8 @@ __device__ __forceinline__ void vjp_tile_view(const T* img, const float2* gimg, 
     // CENTRAL footprints are staged only for central-safe, hence interior,
     // tiles.  With the fused data VJP: the line pass where samples along
     // the ray-parallel axis move by at most BP_VJP_LINE_DU px per voxel
-    // (there it merges most: about 2 du + 0.25 atomics per sample), else
-    // four atomics per sample from the packed loop, far fewer instructions
+    // (there it merges most: about 4 (du + 1/16) atomics per sample), else
+    // four atomics per sample from the packed loop, with fewer instructions
     if (PROJ && BP_VJP_LINES &&
         fminf(fabsf(t.ru[0]), fabsf(t.ru[1])) <= BP_VJP_LINE_DU * t.W0) {
       vjp_view_central2<ZB, E, FDK, false, false, P>(buf, pout, pi.nu, pi.nv, t, ti.dx, ti.dy,
@@ -1323,11 +1332,14 @@ __host__ __device__ constexpr int vjp_smem_bytes() {
 // item % ntiles.  All threads of the CTA call it with the CTA's shared memory.
 template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ, bool STAGE>
 __device__ __forceinline__ void vjp_item(const float* __restrict__ dvol, const T* __restrict__ proj,
-                                         const ProjInfo& pi, const float2* __restrict__ grad,
+                                         const ProjInfo& pi_in, const float2* __restrict__ grad,
                                          const ViewGeom* __restrict__ geom, const VolInfo& vi,
                                          float* __restrict__ partials, float* __restrict__ dproj,
                                          int vchunk, int item, TileView (*tvs)[VB],
                                          float (*red)[NT / 32][12], unsigned char* dyn_smem) {
+  // the projection layout in registers: read once per item (for the batched
+  // launch, from the member table in parameter space) instead of per view
+  const ProjInfo pi = pi_in;
   constexpr bool CONV = STAGE && conv_staging<T>();
   using G = typename std::conditional<CONV, ConvGeom, StageGeom<T>>::type;
   T* bufs = reinterpret_cast<T*>(dyn_smem);  // plain: two buffers of T
@@ -1613,82 +1625,51 @@ cudaError_t launch_vjp_proj(const float* dvol, const ProjInfo& pi, const ViewGeo
 }
 
 // ------------------------------------------------------------------ batches
-// Persistent forms of the forward and the motion VJP over the work items of
-// every member of a batch table: SMs x (resident CTAs per SM) blocks take
-// items from an atomic counter, so the items run in order (CTAs resident at
-// the same time work on neighbouring items: the same view chunk of the VJP,
-// whose data stay in L2) and CTAs that drew cheap items (tiles off the
-// detector) take more.  No CTA waits on another.  Each item runs the per-job
-// block code, so the results are bit for bit those of the per-job launches.
+// The forward and the motion VJP over the work items of every member of a
+// batch.  The member table is a __grid_constant__ parameter, so the tile code
+// reads each job's sizes and pointers from read-only parameter space, as the
+// per-job kernels read their arguments.  Each item runs the per-job block
+// code, so the results are bit for bit those of the per-job launches.
 // Members are staged (checked by the host) in the batch's dtype.
-
-// The next work item for the whole CTA (one atomic add per item), and the
-// descriptor of its job copied to shared memory: the tile code then reads
-// the job's sizes and pointers from there as it needs them, like kernel
-// parameters, instead of holding them in registers.
-__device__ __forceinline__ int next_item(unsigned int* counter, const BatchTable* t,
-                                         const int* off, BatchJob* sj, int* local) {
-  __shared__ int item, job;
-  __syncthreads();  // every thread is done with the previous item
-  if (threadIdx.x == 0) {
-    item = (int)atomicAdd(counter, 1u);
-    job = item < off[t->njobs] ? batch_find(off, t->njobs, item) : 0;
-  }
-  __syncthreads();
-  const int w = item;
-  if (w < off[t->njobs]) {
-    constexpr int NW = (int)(sizeof(BatchJob) / 4);
-    const unsigned* src = reinterpret_cast<const unsigned*>(&t->job[job]);
-    unsigned* dst = reinterpret_cast<unsigned*>(sj);
-    for (int q = threadIdx.x; q < NW; q += blockDim.x) dst[q] = src[q];
-    *local = w - off[job];
-  }
-  __syncthreads();
-  return w;
-}
-
-// The item bodies are called, not inlined, from the persistent loops: each
-// call then allocates registers like one block of the per-job kernel, and
-// the loop's own state is saved once per item instead of competing with the
-// tile code for registers.
-template <int ZB, typename T, bool FDK>
-__device__ __noinline__ void forward_tile_call(const BatchJob* sj, int item, TileView (*tvs)[VB],
-                                               unsigned char* dyn_smem) {
-  forward_tile<ZB, T, FDK, true>((const T*)sj->proj, sj->pi, sj->geom, sj->vif, sj->vol, item, tvs,
-                                 dyn_smem);
-}
-
-template <int ZB, typename T, bool FDK, bool EXACT>
-__device__ __noinline__ void vjp_item_call(const BatchJob* sj, int item, TileView (*tvs)[VB],
-                                           float (*red)[NT / 32][12], unsigned char* dyn_smem) {
-  vjp_item<ZB, T, FDK, EXACT, false, true>(sj->dvol, (const T*)sj->proj, sj->pi, sj->grad, sj->geom,
-                                           sj->vi, sj->partials, nullptr, sj->vchunk, item, tvs,
-                                           red, dyn_smem);
-}
+//
+// The forward is persistent: SMs x (resident CTAs per SM) blocks take tiles
+// from an atomic counter, so tiles run in order (CTAs resident at the same
+// time work on neighbouring tiles) and CTAs that drew cheap tiles (off the
+// detector) take more; no CTA waits on another.  The VJP is a grouped
+// launch, one block per (tile, view chunk) item of the member set, in the
+// per-job kernel's order (the view chunk's data stay in L2).
 
 template <int ZB, typename T, bool FDK>
-__global__ void __launch_bounds__(NT, FWD_MINB) batch_forward_kernel(BatchTable* __restrict__ t) {
+__global__ void __launch_bounds__(NT, FWD_MINB)
+    batch_forward_kernel(const __grid_constant__ BatchTable t, unsigned* __restrict__ counter) {
   __shared__ TileView tvs[2][VB];
-  __shared__ __align__(16) BatchJob sj;
-  __shared__ int local;
+  __shared__ int item;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  const int total = t->off_fwd[t->njobs];
-  for (int w = next_item(&t->next_fwd, t, t->off_fwd, &sj, &local); w < total;
-       w = next_item(&t->next_fwd, t, t->off_fwd, &sj, &local))
-    forward_tile_call<ZB, T, FDK>(&sj, local, tvs, dyn_smem);
+  const int n = t.njobs, total = t.off_fwd[n];
+  for (;;) {
+    __syncthreads();  // every thread is done with the previous tile
+    if (threadIdx.x == 0) item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int w = item;
+    if (w >= total) break;
+    const int j = batch_find(t.off_fwd, n, w);
+    const BatchJob& J = t.job[j];
+    forward_tile<ZB, T, FDK, true>((const T*)J.proj, J.pi, J.geom, J.vif, J.vol, w - t.off_fwd[j],
+                                   tvs, dyn_smem);
+  }
 }
 
 template <int ZB, typename T, bool FDK, bool EXACT>
-__global__ void __launch_bounds__(NT, VJP_MINB) batch_vjp_kernel(BatchTable* __restrict__ t) {
+__global__ void __launch_bounds__(NT, VJP_MINB)
+    batch_vjp_kernel(const __grid_constant__ BatchTable t) {
   __shared__ TileView tvs[2][VB];
   __shared__ float red[2][NT / 32][12];
-  __shared__ __align__(16) BatchJob sj;
-  __shared__ int local;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  const int total = t->off_vjp[t->njobs];
-  for (int w = next_item(&t->next_vjp, t, t->off_vjp, &sj, &local); w < total;
-       w = next_item(&t->next_vjp, t, t->off_vjp, &sj, &local))
-    vjp_item_call<ZB, T, FDK, EXACT>(&sj, local, tvs, red, dyn_smem);
+  const int w = blockIdx.x, j = batch_find(t.off_vjp, t.njobs, w);
+  const BatchJob& J = t.job[j];
+  vjp_item<ZB, T, FDK, EXACT, false, true>(J.dvol, (const T*)J.proj, J.pi, J.grad, J.geom, J.vi,
+                                           J.partials, nullptr, J.vchunk, w - t.off_vjp[j], tvs,
+                                           red, dyn_smem);
 }
 
 int forward_zb() { return ZB_FWD; }
@@ -1699,44 +1680,46 @@ int vjp_view_chunk(const ProjInfo& pi, int dtype, int exact) {
 }
 
 template <typename T, bool FDK>
-static cudaError_t batch_forward_t(BatchTable* tab, int sms, cudaStream_t s) {
+static cudaError_t batch_forward_t(const BatchTable& tab, unsigned* counter, int sms,
+                                   cudaStream_t s) {
   const int smem = fwd_smem_bytes<T>();
   cudaError_t e = smem_attr_once<batch_forward_kernel<ZB_FWD, T, FDK>>(smem);
   if (e != cudaSuccess) return e;
-  batch_forward_kernel<ZB_FWD, T, FDK><<<sms * FWD_MINB, NT, smem, s>>>(tab);
+  batch_forward_kernel<ZB_FWD, T, FDK><<<sms * FWD_MINB, NT, smem, s>>>(tab, counter);
   return cudaGetLastError();
 }
 
 template <typename T, bool FDK, bool EXACT>
-static cudaError_t batch_vjp_t(BatchTable* tab, int sms, cudaStream_t s) {
+static cudaError_t batch_vjp_t(const BatchTable& tab, cudaStream_t s) {
+  const int items = tab.off_vjp[tab.njobs];
+  if (items <= 0) return cudaSuccess;
   const int smem = vjp_smem_bytes<T>();
   cudaError_t e = smem_attr_once<batch_vjp_kernel<ZB_VJP, T, FDK, EXACT>>(smem);
   if (e != cudaSuccess) return e;
-  batch_vjp_kernel<ZB_VJP, T, FDK, EXACT><<<sms * VJP_MINB, NT, smem, s>>>(tab);
+  batch_vjp_kernel<ZB_VJP, T, FDK, EXACT><<<items, NT, smem, s>>>(tab);
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_forward(BatchTable* tab, int dtype, int fdk, int sms, cudaStream_t s) {
-  if (dtype == 0) return fdk ? batch_forward_t<float, true>(tab, sms, s)
-                             : batch_forward_t<float, false>(tab, sms, s);
-  if (dtype == 1) return fdk ? batch_forward_t<__half, true>(tab, sms, s)
-                             : batch_forward_t<__half, false>(tab, sms, s);
-  return fdk ? batch_forward_t<__nv_bfloat16, true>(tab, sms, s)
-             : batch_forward_t<__nv_bfloat16, false>(tab, sms, s);
+cudaError_t launch_batch_forward(const BatchTable& tab, unsigned* counter, int dtype, int fdk,
+                                 int sms, cudaStream_t s) {
+  if (dtype == 0) return fdk ? batch_forward_t<float, true>(tab, counter, sms, s)
+                             : batch_forward_t<float, false>(tab, counter, sms, s);
+  if (dtype == 1) return fdk ? batch_forward_t<__half, true>(tab, counter, sms, s)
+                             : batch_forward_t<__half, false>(tab, counter, sms, s);
+  return fdk ? batch_forward_t<__nv_bfloat16, true>(tab, counter, sms, s)
+             : batch_forward_t<__nv_bfloat16, false>(tab, counter, sms, s);
 }
 
 template <typename T>
-static cudaError_t batch_vjp_dt(int fdk, int exact, BatchTable* tab, int sms, cudaStream_t s) {
-  if (fdk) return exact ? batch_vjp_t<T, true, true>(tab, sms, s)
-                        : batch_vjp_t<T, true, false>(tab, sms, s);
-  return exact ? batch_vjp_t<T, false, true>(tab, sms, s) : batch_vjp_t<T, false, false>(tab, sms, s);
+static cudaError_t batch_vjp_dt(int fdk, int exact, const BatchTable& tab, cudaStream_t s) {
+  if (fdk) return exact ? batch_vjp_t<T, true, true>(tab, s) : batch_vjp_t<T, true, false>(tab, s);
+  return exact ? batch_vjp_t<T, false, true>(tab, s) : batch_vjp_t<T, false, false>(tab, s);
 }
 
-cudaError_t launch_batch_vjp(BatchTable* tab, int dtype, int fdk, int exact, int sms,
-                             cudaStream_t s) {
-  if (dtype == 0) return batch_vjp_dt<float>(fdk, exact, tab, sms, s);
-  if (dtype == 1) return batch_vjp_dt<__half>(fdk, exact, tab, sms, s);
-  return batch_vjp_dt<__nv_bfloat16>(fdk, exact, tab, sms, s);
+cudaError_t launch_batch_vjp(const BatchTable& tab, int dtype, int fdk, int exact, cudaStream_t s) {
+  if (dtype == 0) return batch_vjp_dt<float>(fdk, exact, tab, s);
+  if (dtype == 1) return batch_vjp_dt<__half>(fdk, exact, tab, s);
+  return batch_vjp_dt<__nv_bfloat16>(fdk, exact, tab, s);
 }
 
 // Shared-memory attributes of the batch kernels on the current device (call
