@@ -1332,14 +1332,11 @@ __host__ __device__ constexpr int vjp_smem_bytes() {
 // item % ntiles.  All threads of the CTA call it with the CTA's shared memory.
 template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ, bool STAGE>
 __device__ __forceinline__ void vjp_item(const float* __restrict__ dvol, const T* __restrict__ proj,
-                                         const ProjInfo& pi_in, const float2* __restrict__ grad,
+                                         const ProjInfo& pi, const float2* __restrict__ grad,
                                          const ViewGeom* __restrict__ geom, const VolInfo& vi,
                                          float* __restrict__ partials, float* __restrict__ dproj,
                                          int vchunk, int item, TileView (*tvs)[VB],
                                          float (*red)[NT / 32][12], unsigned char* dyn_smem) {
-  // the projection layout in registers: read once per item (for the batched
-  // launch, from the member table in parameter space) instead of per view
-  const ProjInfo pi = pi_in;
   constexpr bool CONV = STAGE && conv_staging<T>();
   using G = typename std::conditional<CONV, ConvGeom, StageGeom<T>>::type;
   T* bufs = reinterpret_cast<T*>(dyn_smem);  // plain: two buffers of T
