@@ -138,7 +138,7 @@ void bp_ctx_destroy(bp_ctx* ctx) {
                  &ctx->s_P,    &ctx->s_motion, &ctx->s_vw,     &ctx->s_scale,    &ctx->s_vol,
                  &ctx->s_dvol, &ctx->s_out_motion, &ctx->s_out_P, &ctx->s_out_proj,
                  &ctx->s_theta, &ctx->s_grad, &ctx->s_m1,       &ctx->s_m2,       &ctx->s_loss,
-                 &ctx->s_nodes, &ctx->s_out_nodes, &ctx->probe};
+                 &ctx->s_nodes, &ctx->s_out_nodes, &ctx->probe, &ctx->blkimg};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   resolve_timing(ctx);
@@ -155,7 +155,7 @@ long long bp_ctx_workspace_bytes(const bp_ctx* ctx) {
                        &ctx->s_P,    &ctx->s_motion, &ctx->s_vw,     &ctx->s_scale,    &ctx->s_vol,
                        &ctx->s_dvol, &ctx->s_out_motion, &ctx->s_out_P, &ctx->s_out_proj,
                        &ctx->s_theta, &ctx->s_grad, &ctx->s_m1,       &ctx->s_m2,       &ctx->s_loss,
-                       &ctx->s_nodes, &ctx->s_out_nodes, &ctx->probe};
+                       &ctx->s_nodes, &ctx->s_out_nodes, &ctx->probe, &ctx->blkimg};
   long long t = 0;
   for (const Buf* b : bufs) t += (long long)b->n;
   return t;
@@ -337,11 +337,20 @@ int bp_vjp(bp_ctx* ctx, const float* dL_dvol, const void* proj, const bp_proj_de
     }
     if (nvox > 0) {
       CK(ensure(ctx->partials, sizeof(float) * bpk::PSLOTS * (size_t)V * ntiles), "alloc partials");
-      CK(TL(fuse ? K_VJP_FUSED : K_VJP_MOTION, 1,
+      // the fused data VJP of staged CENTRAL tiles goes through a block
+      // image (one vector reduction per sample), added into dL_dproj by a
+      // second kernel of the same launch
+      const bool blocks = fuse && bpk::vjp_uses_blocks(dproj, pdesc->dtype, pi,
+                                                       deriv == BP_DERIV_BILINEAR_EXACT);
+      if (blocks)
+        CK(ensure(ctx->blkimg, sizeof(float) * (size_t)bpk::block_image_floats(pi)),
+           "alloc block image");
+      CK(TL(fuse ? K_VJP_FUSED : K_VJP_MOTION, blocks ? 2 : 1,
             bpk::launch_vjp_motion(ddvol, dproj, pdesc->dtype, pi, grad,
                                    (const ViewGeom*)ctx->geom.p, vi, weight == BP_WEIGHT_FDK,
                                    deriv == BP_DERIV_BILINEAR_EXACT, (float*)ctx->partials.p,
-                                   fuse ? (float*)oD : nullptr, s)),
+                                   fuse ? (float*)oD : nullptr,
+                                   blocks ? (float*)ctx->blkimg.p : nullptr, s)),
          "vjp kernel");
     }
     CK(TL(K_REDUCE, 1, bpk::launch_reduce_chain((const float*)ctx->partials.p, nvox > 0 ? ntiles : 0,
@@ -352,8 +361,12 @@ int bp_vjp(bp_ctx* ctx, const float* dL_dvol, const void* proj, const bp_proj_de
     ProjInfo po = pi;
     po.rs = pdesc->nu;
     po.vs = (long long)pdesc->nu * pdesc->nv;
-    CK(TL(K_VJP_PROJ, 1, bpk::launch_vjp_proj(ddvol, po, (const ViewGeom*)ctx->geom.p, vi,
-                                              weight == BP_WEIGHT_FDK, (float*)oD, s)),
+    const long long bf = bpk::block_image_floats(po);
+    if (bf > 0) CK(ensure(ctx->blkimg, sizeof(float) * (size_t)bf), "alloc block image");
+    CK(TL(K_VJP_PROJ, bf > 0 ? 2 : 1,
+          bpk::launch_vjp_proj(ddvol, po, (const ViewGeom*)ctx->geom.p, vi,
+                               weight == BP_WEIGHT_FDK, (float*)oD,
+                               bf > 0 ? (float*)ctx->blkimg.p : nullptr, s)),
        "proj vjp kernel");
   }
   if (hm) CK(cudaMemcpyAsync(dL_dmotion, om, sizeof(double) * 6 * V, cudaMemcpyDeviceToHost, s), "copy out");

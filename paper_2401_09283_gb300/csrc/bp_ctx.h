@@ -41,7 +41,7 @@ struct bp_ctx {
   double total_ms[bpctx::K_COUNT] = {};
   long long count[bpctx::K_COUNT] = {};
   // workspace
-  bpctx::Buf geom, grad, partials, shblk, fdk_tab, probe;
+  bpctx::Buf geom, grad, partials, shblk, fdk_tab, probe, blkimg;
   // staging of host arguments
   bpctx::Buf s_proj, s_P, s_motion, s_vw, s_scale, s_vol, s_dvol, s_out_motion, s_out_P, s_out_proj,
       s_theta, s_grad, s_m1, s_m2, s_loss, s_nodes, s_out_nodes;

@@ -98,17 +98,25 @@ cudaError_t launch_grad_images(const void* proj, int dtype, const ProjInfo& pi, 
                                cudaStream_t s);
 
 // dproj != NULL fuses the data VJP (same samples, contiguous [V][nv][nu]
-// output zeroed by the caller) into the motion-VJP kernel.
+// output zeroed by the caller) into the motion-VJP kernel.  blk (NULL or
+// block_image_floats(pi) floats of scratch) is the block image of the staged
+// CENTRAL scatter (per pixel, the 2x2 block it starts, 16 bytes); when
+// vjp_uses_blocks() the launch zeroes it, runs the VJP and then a second
+// kernel that adds it into dproj.
 cudaError_t launch_vjp_motion(const float* dvol, const void* proj, int dtype, const ProjInfo& pi,
                               const float2* grad, const ViewGeom* geom, const VolInfo& vi,
-                              int fdk, int exact, float* partials, float* dproj, cudaStream_t s);
+                              int fdk, int exact, float* partials, float* dproj, float* blk,
+                              cudaStream_t s);
+long long block_image_floats(const ProjInfo& pi);
+bool vjp_uses_blocks(const void* proj, int dtype, const ProjInfo& pi, int exact);
 
 cudaError_t launch_reduce_chain(const float* partials, int ntiles, const VolInfo& vi,
                                 const double* P, const double* theta, int V, double* dL_dPhat,
                                 double* dL_dtheta, cudaStream_t s);
 
+// Data VJP alone; blk (NULL or block_image_floats(pi) floats) as above.
 cudaError_t launch_vjp_proj(const float* dvol, const ProjInfo& pi, const ViewGeom* geom,
-                            const VolInfo& vi, int fdk, float* dproj, cudaStream_t s);
+                            const VolInfo& vi, int fdk, float* dproj, float* blk, cudaStream_t s);
 
 cudaError_t launch_sharpness(const float* vol, int nx, int ny, int nz, double* block_sums,
                              int max_blocks, double* loss, float* grad, cudaStream_t s);

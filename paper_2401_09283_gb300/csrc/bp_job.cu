@@ -142,7 +142,7 @@ cudaError_t record_iteration(bp_job* j, cudaStream_t s) {
                                    j->hist, j->iter, j->max_iters, j->dvol, s);
   if (e != cudaSuccess) return e;
   e = bpk::launch_vjp_motion(j->dvol, j->proj, j->pd.dtype, j->pi, j->grad, j->geom, j->vi, fdk,
-                             j->deriv == BP_DERIV_BILINEAR_EXACT, j->partials, nullptr, s);
+                             j->deriv == BP_DERIV_BILINEAR_EXACT, j->partials, nullptr, nullptr, s);
   if (e != cudaSuccess) return e;
   e = bpk::launch_reduce_chain(j->partials, j->ntiles, j->vi, j->P, j->theta, V, nullptr, j->gth,
                                s);

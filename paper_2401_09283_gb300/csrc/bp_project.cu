@@ -869,6 +869,62 @@ __device__ __forceinline__ void scatter_sample(float* out, int nu, int nv, const
   }
 }
 
+// ----------------------------------------------- block image (fused data VJP)
+
+// The fused data VJP of interior tiles adds a sample's four bilinear weights
+// with ONE 16-byte vector reduction instead of four scalar ones, into a block
+// image: entry (r, c) holds the 2x2 pixel block with top-left pixel (r, c) as
+// 4 consecutive floats, (r,c), (r,c+1), (r+1,c), (r+1,c+1), so a sample whose
+// floor pixel is (iu, iv) adds to entry iv*nu + iu, a 16-byte aligned
+// address with the same index arithmetic as the pixel itself.
+// block_combine_kernel adds the blocks into dL/dproj afterwards (pixel (r, c)
+// is element (dr, dc) of the entries (r-dr, c-dc)).
+#ifndef BP_VJP_BLOCKS
+#define BP_VJP_BLOCKS 1
+#endif
+
+__device__ __forceinline__ void red_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
+}
+
+// dproj[v][r][c] += the four block entries covering pixel (r, c): element 0
+// of (r, c), 1 of (r, c-1), 2 of (r-1, c), 3 of (r-1, c-1).  One CTA per
+// detector row.
+__global__ void __launch_bounds__(256) block_combine_kernel(const float* __restrict__ blk,
+                                                           float* __restrict__ dproj, int nv,
+                                                           int nu) {
+  const long long row = blockIdx.x;  // v * nv + r
+  const bool up = row % nv != 0;
+  const float* q0 = blk + row * nu * 4;
+  const float* q1 = q0 - (long long)nu * 4;
+  float* out = dproj + row * nu;
+  for (int c = threadIdx.x; c < nu; c += blockDim.x) {
+    float acc = __ldg(q0 + 4 * c);
+    if (c > 0) acc += __ldg(q0 + 4 * (c - 1) + 1);
+    if (up) {
+      acc += __ldg(q1 + 4 * c + 2);
+      if (c > 0) acc += __ldg(q1 + 4 * (c - 1) + 3);
+    }
+    out[c] += acc;
+  }
+}
+
+long long block_image_floats(const ProjInfo& pi) {
+  if (!BP_VJP_BLOCKS) return 0;
+  return (long long)pi.nviews * pi.nv * pi.nu * 4;
+}
+
+cudaError_t launch_block_combine(const float* blk, const ProjInfo& pi, float* dproj,
+                                cudaStream_t s) {
+  const long long rows = (long long)pi.nviews * pi.nv;
+  if (rows <= 0 || pi.nu <= 0) return cudaSuccess;
+  if (rows > 0x7fffffffLL) return cudaErrorInvalidValue;
+  block_combine_kernel<<<(unsigned)rows, 256, 0, s>>>(blk, dproj, pi.nv, pi.nu);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------- VJP w.r.t. Phat
 
 // Sum of 16 per-lane values over the warp, scattered: lane l ends with the
@@ -1028,8 +1084,8 @@ __device__ __forceinline__ void vjp_view(const T* img, const float2* gimg, const
 // negation instruction is needed.  Even and odd voxels are summed in the two
 // halves of the pair accumulators and added at the end.
 template <int ZB, typename T, bool FDK, bool EDGE, bool PROJ, int P = StageGeom<T>::P>
-__device__ __forceinline__ void vjp_view_central2(const T* buf, float* pout, int nu, int nv,
-                                                  const TileView& t, float dx, float dy,
+__device__ __forceinline__ void vjp_view_central2(const T* buf, float* pout, float* qout, int nu,
+                                                  int nv, const TileView& t, float dx, float dy,
                                                   const float (&delta)[ZB], float (&S)[3],
                                                   float (&Z)[3]) {
   
@@ -1109,7 +1165,12 @@ __device__ __forceinline__ void vjp_view_central2(const T* buf, float* pout, int
         byi = iv + MAGIC_BITS - t.av;
 #endif
         // (iv * nu + iu) from the floor bits, in 32-bit wraparound arithmetic
-        float* q = pout + ((unsigned)byi * (unsigned)nu + (unsigned)bxi + pofs);
+        const unsigned px = (unsigned)byi * (unsigned)nu + (unsigned)bxi + pofs;
+        if (BP_VJP_BLOCKS && qout) {  // one vector reduction into the block image
+          red_v4(qout + 4 * px, w[0][h], w[1][h], w[2][h], w[3][h]);
+          continue;
+        }
+        float* q = pout + px;
         atomicAdd(q, w[0][h]);
         atomicAdd(q + 1, w[1][h]);
         atomicAdd(q + nu, w[2][h]);
@@ -1147,7 +1208,8 @@ __device__ __forceinline__ void vjp_view_central2(const T* buf, float* pout, int
 // same weights, summed in another order.  dsm holds the tile's dL/dvol as
 // [z][y][x] with a row pitch of TX + 1.
 template <int ZB, bool FDK>
-__device__ __forceinline__ void proj_lines(float* __restrict__ pout, int nu, const TileView& t,
+__device__ __forceinline__ void proj_lines(float* __restrict__ pout, float* __restrict__ qout,
+                                           int nu, int nv, const TileView& t,
                                            const float* __restrict__ dsm) {
   static_assert(ZB == TX && TY == TX, "lines run along a 16-voxel tile edge");
   const int a = threadIdx.x & (TX - 1), b = threadIdx.x / TX;
@@ -1207,13 +1269,18 @@ __device__ __forceinline__ void proj_lines(float* __restrict__ pout, int nu, con
       const bool keep = have && bx == cb && by == rb;
       if (have && !keep) {  // the line leaves the open cell: add its four pixels
         int fc = cb - MAGIC_BITS + t.au, fr = rb - MAGIC_BITS + t.av;
-        bc_interior(BC_SCATTER, fc, fr, nu, 1 << 30);
-        float* q = pout + ((unsigned)(fr + MAGIC_BITS - t.av) * (unsigned)nu +
-                           (unsigned)(fc + MAGIC_BITS - t.au) + pofs);
-        atomicAdd(q, a0);
-        atomicAdd(q + 1, a1);
-        atomicAdd(q + nu, b0);
-        atomicAdd(q + nu + 1, b1);
+        bc_interior(BC_SCATTER, fc, fr, nu, nv);
+        const unsigned px = (unsigned)(fr + MAGIC_BITS - t.av) * (unsigned)nu +
+                            (unsigned)(fc + MAGIC_BITS - t.au) + pofs;
+        if (BP_VJP_BLOCKS && qout) {
+          red_v4(qout + 4 * px, a0, a1, b0, b1);
+        } else {
+          float* q = pout + px;
+          atomicAdd(q, a0);
+          atomicAdd(q + 1, a1);
+          atomicAdd(q + nu, b0);
+          atomicAdd(q + nu + 1, b1);
+        }
       }
       a0 = (keep ? a0 : 0.0f) + ww[0][h];
       a1 = (keep ? a1 : 0.0f) + ww[1][h];
@@ -1225,9 +1292,14 @@ __device__ __forceinline__ void proj_lines(float* __restrict__ pout, int nu, con
     }
   }
   int fc = cb - MAGIC_BITS + t.au, fr = rb - MAGIC_BITS + t.av;
-  bc_interior(BC_SCATTER, fc, fr, nu, 1 << 30);
-  float* q = pout + ((unsigned)(fr + MAGIC_BITS - t.av) * (unsigned)nu +
-                     (unsigned)(fc + MAGIC_BITS - t.au) + pofs);
+  bc_interior(BC_SCATTER, fc, fr, nu, nv);
+  const unsigned px = (unsigned)(fr + MAGIC_BITS - t.av) * (unsigned)nu +
+                      (unsigned)(fc + MAGIC_BITS - t.au) + pofs;
+  if (BP_VJP_BLOCKS && qout) {
+    red_v4(qout + 4 * px, a0, a1, b0, b1);
+    return;
+  }
+  float* q = pout + px;
   atomicAdd(q, a0);
   atomicAdd(q + 1, a1);
   atomicAdd(q + nu, b0);
@@ -1241,8 +1313,9 @@ __device__ __forceinline__ void proj_lines(float* __restrict__ pout, int nu, con
 // data VJP per sample.
 template <int ZB, typename T, bool FDK, bool EXACT, bool PROJ, typename E, int P>
 __device__ __forceinline__ void vjp_tile_view(const T* img, const float2* gimg, const E* buf,
-                                              bool staged, float* pout, const ProjInfo& pi,
-                                              const TileView& t, const TileIdx& ti,
+                                              bool staged, float* pout, float* qout,
+                                              const ProjInfo& pi, const TileView& t,
+                                              const TileIdx& ti,
                                               const float (&delta)[ZB], const float* dsm,
                                               float (*redv)[12]) {
   float S[3] = {0.0f, 0.0f, 0.0f}, Z[3] = {0.0f, 0.0f, 0.0f};
@@ -1254,11 +1327,11 @@ __device__ __forceinline__ void vjp_tile_view(const T* img, const float2* gimg, 
     // four atomics per sample from the packed loop, with fewer instructions
     if (PROJ && BP_VJP_LINES &&
         fminf(fabsf(t.ru[0]), fabsf(t.ru[1])) <= BP_VJP_LINE_DU * t.W0) {
-      vjp_view_central2<ZB, E, FDK, false, false, P>(buf, pout, pi.nu, pi.nv, t, ti.dx, ti.dy,
+      vjp_view_central2<ZB, E, FDK, false, false, P>(buf, pout, qout, pi.nu, pi.nv, t, ti.dx, ti.dy,
                                                      delta, S, Z);
-      proj_lines<ZB, FDK>(pout, pi.nu, t, dsm);
+      proj_lines<ZB, FDK>(pout, qout, pi.nu, pi.nv, t, dsm);
     } else {
-      vjp_view_central2<ZB, E, FDK, false, PROJ, P>(buf, pout, pi.nu, pi.nv, t, ti.dx, ti.dy,
+      vjp_view_central2<ZB, E, FDK, false, PROJ, P>(buf, pout, qout, pi.nu, pi.nv, t, ti.dx, ti.dy,
                                                     delta, S, Z);
     }
   } else if (staged) {
@@ -1335,7 +1408,7 @@ __device__ __forceinline__ void vjp_item(const float* __restrict__ dvol, const T
                                          const ProjInfo& pi, const float2* __restrict__ grad,
                                          const ViewGeom* __restrict__ geom, const VolInfo& vi,
                                          float* __restrict__ partials, float* __restrict__ dproj,
-                                         int vchunk, int item, TileView (*tvs)[VB],
+                                         float* __restrict__ dblk, int vchunk, int item, TileView (*tvs)[VB],
                                          float (*red)[NT / 32][12], unsigned char* dyn_smem) {
   constexpr bool CONV = STAGE && conv_staging<T>();
   using G = typename std::conditional<CONV, ConvGeom, StageGeom<T>>::type;
@@ -1420,13 +1493,15 @@ __device__ __forceinline__ void vjp_item(const float* __restrict__ dvol, const T
       const T* img = proj + (long long)v * pi.vs;
       const float2* gimg = EXACT ? nullptr : grad + (long long)v * pi.nv * pi.nu;
       float* pout = PROJ ? dproj + (long long)v * pi.nv * pi.nu : nullptr;
+      float* qout =
+          PROJ && dblk ? dblk + (long long)v * 4 * pi.nv * pi.nu : nullptr;
       if constexpr (CONV)
-        vjp_tile_view<ZB, T, FDK, EXACT, PROJ, float, CONV_P>(img, gimg, F, t.staged, pout, pi, t,
-                                                              ti, delta, dsm, red[idx & 1]);
+        vjp_tile_view<ZB, T, FDK, EXACT, PROJ, float, CONV_P>(img, gimg, F, t.staged, pout, qout,
+                                                              pi, t, ti, delta, dsm, red[idx & 1]);
       else
         vjp_tile_view<ZB, T, FDK, EXACT, PROJ, T, StageGeom<T>::P>(
-            img, gimg, bufs + (idx & 1) * CAP, STAGE && t.staged, pout, pi, t, ti, delta, dsm,
-            red[idx & 1]);
+            img, gimg, bufs + (idx & 1) * CAP, STAGE && t.staged, pout, qout, pi, t, ti, delta,
+            dsm, red[idx & 1]);
     }
     if constexpr (CONV) cp_async_wait0();  // the raw copy of view v+1
     __syncthreads();  // F and the staging buffers are free; red[idx & 1] complete
@@ -1443,12 +1518,12 @@ __global__ void __launch_bounds__(NT, VJP_MINB)
     vjp_motion_kernel(const float* __restrict__ dvol, const T* __restrict__ proj, ProjInfo pi,
                       const float2* __restrict__ grad, const ViewGeom* __restrict__ geom,
                       VolInfo vi, float* __restrict__ partials, float* __restrict__ dproj,
-                      int vchunk) {
+                      float* __restrict__ dblk, int vchunk) {
   __shared__ TileView tvs[2][VB];
   __shared__ float red[2][NT / 32][12];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  vjp_item<ZB, T, FDK, EXACT, PROJ, STAGE>(dvol, proj, pi, grad, geom, vi, partials, dproj, vchunk,
-                                           blockIdx.x, tvs, red, dyn_smem);
+  vjp_item<ZB, T, FDK, EXACT, PROJ, STAGE>(dvol, proj, pi, grad, geom, vi, partials, dproj, dblk,
+                                           vchunk, blockIdx.x, tvs, red, dyn_smem);
 }
 
 #ifndef BP_VJP_CHUNK_MIB
@@ -1469,36 +1544,54 @@ static int view_chunk(const ProjInfo& pi, long long bytes_per_px) {
 template <typename T, bool FDK, bool EXACT, bool PROJ, bool STAGE>
 static cudaError_t vjp_launch(const float* dvol, const void* proj, const ProjInfo& pi,
                               const float2* grad, const ViewGeom* geom, const VolInfo& vi,
-                              float* partials, float* dproj, int vc, unsigned nblocks,
-                              cudaStream_t s) {
+                              float* partials, float* dproj, float* blk, int vc,
+                              unsigned nblocks, cudaStream_t s) {
   const int smem = STAGE ? vjp_smem_bytes<T, PROJ && !EXACT && BP_VJP_LINES>() : 0;
   if (STAGE) {
     cudaError_t e = smem_attr_once<vjp_motion_kernel<ZB_VJP, T, FDK, EXACT, PROJ, STAGE>>(smem);
     if (e != cudaSuccess) return e;
   }
   vjp_motion_kernel<ZB_VJP, T, FDK, EXACT, PROJ, STAGE><<<nblocks, NT, smem, s>>>(
-      dvol, (const T*)proj, pi, grad, geom, vi, partials, dproj, vc);
+      dvol, (const T*)proj, pi, grad, geom, vi, partials, dproj, blk, vc);
   return cudaGetLastError();
 }
 
 template <typename T, bool FDK, bool EXACT>
 static cudaError_t vjp_dispatch(const float* dvol, const void* proj, const ProjInfo& pi,
                                 const float2* grad, const ViewGeom* geom, const VolInfo& vi,
-                                float* partials, float* dproj, cudaStream_t s) {
+                                float* partials, float* dproj, float* blk, cudaStream_t s) {
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
-  const long long bpp = (long long)sizeof(T) + (EXACT ? 0 : 8) + (dproj ? 4 : 0);
+  const bool stage = stageable<T>(proj, pi);
+  // block images only where the staged CENTRAL paths scatter
+  const bool useb = dproj && blk && stage && !EXACT && BP_VJP_BLOCKS;
+  const long long bpp =
+      (long long)sizeof(T) + (EXACT ? 0 : 8) + (dproj ? 4 : 0) + (useb ? 16 : 0);
   const int vc = view_chunk(pi, bpp);
   const unsigned nblocks = (unsigned)((long long)ntiles * ((pi.nviews + vc - 1) / vc));
-  const bool stage = stageable<T>(proj, pi);
-  if (dproj)
-    return stage ? vjp_launch<T, FDK, EXACT, true, true>(dvol, proj, pi, grad, geom, vi, partials,
-                                                         dproj, vc, nblocks, s)
-                 : vjp_launch<T, FDK, EXACT, true, false>(dvol, proj, pi, grad, geom, vi,
-                                                          partials, dproj, vc, nblocks, s);
+  if (dproj) {
+    cudaError_t e = cudaSuccess;
+    if (useb) e = cudaMemsetAsync(blk, 0, sizeof(float) * (size_t)block_image_floats(pi), s);
+    if (e == cudaSuccess)
+      e = stage ? vjp_launch<T, FDK, EXACT, true, true>(dvol, proj, pi, grad, geom, vi, partials,
+                                                        dproj, useb ? blk : nullptr, vc, nblocks,
+                                                        s)
+                : vjp_launch<T, FDK, EXACT, true, false>(dvol, proj, pi, grad, geom, vi,
+                                                         partials, dproj, nullptr, vc, nblocks, s);
+    if (e == cudaSuccess && useb) e = launch_block_combine(blk, pi, dproj, s);
+    return e;
+  }
   return stage ? vjp_launch<T, FDK, EXACT, false, true>(dvol, proj, pi, grad, geom, vi, partials,
-                                                        nullptr, vc, nblocks, s)
+                                                        nullptr, nullptr, vc, nblocks, s)
                : vjp_launch<T, FDK, EXACT, false, false>(dvol, proj, pi, grad, geom, vi,
-                                                         partials, nullptr, vc, nblocks, s);
+                                                         partials, nullptr, nullptr, vc, nblocks,
+                                                         s);
+}
+
+bool vjp_uses_blocks(const void* proj, int dtype, const ProjInfo& pi, int exact) {
+  if (exact || !BP_VJP_BLOCKS) return false;
+  if (dtype == 0) return stageable<float>(proj, pi);
+  if (dtype == 1) return stageable<__half>(proj, pi);
+  return stageable<__nv_bfloat16>(proj, pi);
 }
 
 // Set the VJP kernels' shared-memory attributes on the current device
@@ -1524,37 +1617,46 @@ template <typename T>
 static cudaError_t vjp_dispatch_t(int fdk, int exact, const float* dvol, const void* proj,
                                   const ProjInfo& pi, const float2* grad, const ViewGeom* geom,
                                   const VolInfo& vi, float* partials, float* dproj,
-                                  cudaStream_t s) {
+                                  float* blk, cudaStream_t s) {
   if (fdk)
-    return exact ? vjp_dispatch<T, true, true>(dvol, proj, pi, grad, geom, vi, partials, dproj, s)
-                 : vjp_dispatch<T, true, false>(dvol, proj, pi, grad, geom, vi, partials, dproj, s);
-  return exact ? vjp_dispatch<T, false, true>(dvol, proj, pi, grad, geom, vi, partials, dproj, s)
-               : vjp_dispatch<T, false, false>(dvol, proj, pi, grad, geom, vi, partials, dproj, s);
+    return exact ? vjp_dispatch<T, true, true>(dvol, proj, pi, grad, geom, vi, partials, dproj,
+                                               blk, s)
+                 : vjp_dispatch<T, true, false>(dvol, proj, pi, grad, geom, vi, partials, dproj,
+                                                blk, s);
+  return exact ? vjp_dispatch<T, false, true>(dvol, proj, pi, grad, geom, vi, partials, dproj,
+                                              blk, s)
+               : vjp_dispatch<T, false, false>(dvol, proj, pi, grad, geom, vi, partials, dproj,
+                                               blk, s);
 }
 
 cudaError_t launch_vjp_motion(const float* dvol, const void* proj, int dtype, const ProjInfo& pi,
                               const float2* grad, const ViewGeom* geom, const VolInfo& vi,
-                              int fdk, int exact, float* partials, float* dproj, cudaStream_t s) {
+                              int fdk, int exact, float* partials, float* dproj, float* blk,
+                              cudaStream_t s) {
   if (vi.zb != ZB_VJP) return cudaErrorInvalidValue;
   if (dtype == 0)
-    return vjp_dispatch_t<float>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, dproj, s);
+    return vjp_dispatch_t<float>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, dproj, blk,
+                                 s);
   if (dtype == 1)
-    return vjp_dispatch_t<__half>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, dproj, s);
+    return vjp_dispatch_t<__half>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials, dproj,
+                                  blk, s);
   return vjp_dispatch_t<__nv_bfloat16>(fdk, exact, dvol, proj, pi, grad, geom, vi, partials,
-                                       dproj, s);
+                                       dproj, blk, s);
 }
 
 // ------------------------------------------------- VJP w.r.t. the data
 
 // Adjoint of Eq. 3 in d_j: every voxel-view adds s = delta * c * omega times
 // its four bilinear weights to four detector pixels of a contiguous
-// [V][nv][nu] FP32 image (zeroed by the caller), with scalar global FP32
-// atomics reduced in L2.  (Measured on GB300: shared-memory FP32 atomics are
-// emulated and float4 vector atomics of mostly-zero lanes cost more L2
-// requests than scalar ones, so neither is used.)
+// [V][nv][nu] FP32 image (zeroed by the caller), with global FP32 atomics
+// reduced in L2: on interior tiles one vector reduction into the block image
+// bout (when given), else four scalar ones.  (Measured on GB300: shared-memory
+// FP32 atomics are emulated, and vector atomics with zero lanes cost as much
+// as full ones, so neither privatisation nor padded vectors are used.)
 template <int ZB, bool FDK, bool EDGE>
-__device__ __forceinline__ void proj_view(float* out, int nu, int nv, const TileView& t, float dx,
-                                          float dy, const float (&delta)[ZB]) {
+__device__ __forceinline__ void proj_view(float* out, float* bout, int nu, int nv,
+                                          const TileView& t, float dx, float dy,
+                                          const float (&delta)[ZB]) {
   const float u0 = fmaf(dy, t.ru[1], fmaf(dx, t.ru[0], t.U0));
   const float v0 = fmaf(dy, t.rv[1], fmaf(dx, t.rv[0], t.V0));
   const float w0 = fmaf(dy, t.rw[1], fmaf(dx, t.rw[0], t.W0));
@@ -1566,14 +1668,22 @@ __device__ __forceinline__ void proj_view(float* out, int nu, int nv, const Tile
                             t, nu, nv);
     if (EDGE && !s.ok) continue;
     const float sd = delta[k] * (FDK ? s.rwi * (s.rwi * t.wgtd) : t.wgtd);
-    scatter_sample<EDGE>(out, nu, nv, s, sd);
+    if (!EDGE && BP_VJP_BLOCKS && bout) {
+      int iu = s.iu, iv = s.iv;
+      bc_interior(BC_SCATTER, iu, iv, nu, nv);
+      const float b1 = sd * s.tv, b0 = sd - b1;
+      const float w11 = b1 * s.tu, w01 = b1 - w11, w10 = b0 * s.tu, w00 = b0 - w10;
+      red_v4(bout + 4 * ((long long)iv * nu + iu), w00, w10, w01, w11);
+    } else {
+      scatter_sample<EDGE>(out, nu, nv, s, sd);
+    }
   }
 }
 
 template <int ZB, bool FDK>
 __global__ void __launch_bounds__(NT, 2)
     vjp_proj_kernel(const float* __restrict__ dvol, ProjInfo pi, const ViewGeom* __restrict__ geom,
-                    VolInfo vi, float* __restrict__ dproj, int vchunk) {
+                    VolInfo vi, float* __restrict__ dproj, float* __restrict__ blk, int vchunk) {
   __shared__ TileView tvs[VB];
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
   const int tile = blockIdx.x % ntiles;
@@ -1600,25 +1710,33 @@ __global__ void __launch_bounds__(NT, 2)
       const TileView t = tvs[b];
       if (t.mode == MODE_SKIP) continue;
       float* out = dproj + (long long)(j0 + b) * pi.nv * pi.nu;
+      float* bout = blk ? blk + (long long)(j0 + b) * pi.nv * pi.nu * 4 : nullptr;
       if (t.mode == MODE_INTERIOR)
-        proj_view<ZB, FDK, false>(out, pi.nu, pi.nv, t, ti.dx, ti.dy, delta);
+        proj_view<ZB, FDK, false>(out, bout, pi.nu, pi.nv, t, ti.dx, ti.dy, delta);
       else
-        proj_view<ZB, FDK, true>(out, pi.nu, pi.nv, t, ti.dx, ti.dy, delta);
+        proj_view<ZB, FDK, true>(out, bout, pi.nu, pi.nv, t, ti.dx, ti.dy, delta);
     }
   }
 }
 
 cudaError_t launch_vjp_proj(const float* dvol, const ProjInfo& pi, const ViewGeom* geom,
-                            const VolInfo& vi, int fdk, float* dproj, cudaStream_t s) {
+                            const VolInfo& vi, int fdk, float* dproj, float* blk, cudaStream_t s) {
   if (vi.zb != ZB_VJP) return cudaErrorInvalidValue;
+  if (!BP_VJP_BLOCKS) blk = nullptr;
   const int ntiles = vi.tiles_x * vi.tiles_y * vi.tiles_z;
-  const int vc = view_chunk(pi, 4);
+  const int vc = view_chunk(pi, blk ? 20 : 4);
   const unsigned nblocks = (unsigned)((long long)ntiles * ((pi.nviews + vc - 1) / vc));
+  if (blk) {
+    cudaError_t e = cudaMemsetAsync(blk, 0, sizeof(float) * (size_t)block_image_floats(pi), s);
+    if (e != cudaSuccess) return e;
+  }
   if (fdk)
-    vjp_proj_kernel<ZB_VJP, true><<<nblocks, NT, 0, s>>>(dvol, pi, geom, vi, dproj, vc);
+    vjp_proj_kernel<ZB_VJP, true><<<nblocks, NT, 0, s>>>(dvol, pi, geom, vi, dproj, blk, vc);
   else
-    vjp_proj_kernel<ZB_VJP, false><<<nblocks, NT, 0, s>>>(dvol, pi, geom, vi, dproj, vc);
-  return cudaGetLastError();
+    vjp_proj_kernel<ZB_VJP, false><<<nblocks, NT, 0, s>>>(dvol, pi, geom, vi, dproj, blk, vc);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && blk) e = launch_block_combine(blk, pi, dproj, s);
+  return e;
 }
 
 // ------------------------------------------------------------------ batches
@@ -1665,7 +1783,7 @@ __global__ void __launch_bounds__(NT, VJP_MINB)
   const int w = blockIdx.x, j = batch_find(t.off_vjp, t.njobs, w);
   const BatchJob& J = t.job[j];
   vjp_item<ZB, T, FDK, EXACT, false, true>(J.dvol, (const T*)J.proj, J.pi, J.grad, J.geom, J.vi,
-                                           J.partials, nullptr, J.vchunk, w - t.off_vjp[j], tvs,
+                                           J.partials, nullptr, nullptr, J.vchunk, w - t.off_vjp[j], tvs,
                                            red, dyn_smem);
 }
 
