@@ -349,17 +349,18 @@ int bp_job_wait(const bp_job* job, double timeout_ms);
 int bp_job_iterations_queued(const bp_job* job);
 
 /* ---------------------------------------------------------------- batches
- * Several resident jobs advanced together (the serving form): each stage of
- * an iteration -- compose (Eq. 1), backprojection (Eq. 3), loss, motion VJP
- * (Eqs. 4-5), FP64 reduction and chain (Eq. 2), update -- is ONE persistent
- * launch whose blocks walk the work items (views, tiles, (tile, view chunk)
- * pairs, loss chunks) of every member, so jobs of different volume and view
- * counts share each kernel and fill the GPU together.  The member table is a
- * kernel parameter; each member set gets one captured CUDA graph of the
- * iteration (made at the first step after the set changes; the graph of an
- * earlier set is freed once its queued replays have run).  Every item runs
- * the per-job arithmetic: a member's iterations are bit for bit those of
- * motion_step.
+ * Several resident jobs advanced together (the serving form): compose
+ * (Eq. 1), backprojection (Eq. 3), loss, FP64 reduction and chain (Eq. 2)
+ * and update are each ONE launch whose blocks walk the work items (views,
+ * tiles, loss chunks) of every member -- the backprojection a persistent
+ * kernel -- so jobs of different volume and view counts share each kernel
+ * and fill the GPU together; the motion VJP (Eqs. 4-5) runs each member's
+ * own VJP kernel on a parallel branch of the same graph, so the members'
+ * VJPs overlap.  The member table is a kernel parameter; each member set
+ * gets one captured CUDA graph of the iteration (made at the first step
+ * after the set changes; the graph of an earlier set is freed once its
+ * queued replays have run).  Every item runs the per-job arithmetic: a
+ * member's iterations are bit for bit those of motion_step.
  * Members must share dtype, weight, derivative mode, loss and optimiser,
  * use per-view motion (motion_nodes = 0) and have detector rows of a
  * multiple of 16 bytes; a job is a member of at most one batch and is not

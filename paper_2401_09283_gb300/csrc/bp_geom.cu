@@ -622,7 +622,8 @@ __global__ void batch_opt_kernel(const __grid_constant__ BatchTable t) {
 }
 
 cudaError_t launch_batch_iteration(const BatchTable& tab, unsigned* counter, int dtype, int fdk,
-                                   int exact, int loss, int opt, int sms, cudaStream_t s) {
+                                   int exact, int loss, int opt, int sms, cudaStream_t s,
+                                   const BatchBranches* br) {
   batch_compose_kernel<<<sms, 128, 0, s>>>(tab, fdk, counter);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -638,7 +639,22 @@ cudaError_t launch_batch_iteration(const BatchTable& tab, unsigned* counter, int
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_batch_vjp(tab, dtype, fdk, exact, s);
+  if (br && tab.njobs > 0 && br->n >= tab.njobs) {
+    // each member's VJP kernel (the per-job launch, with its own constant
+    // parameters) on a branch of its own
+    e = cudaEventRecord(br->fork, s);
+    for (int m = 0; m < tab.njobs && e == cudaSuccess; ++m) {
+      const BatchJob& J = tab.job[m];
+      e = cudaStreamWaitEvent(br->streams[m], br->fork, 0);
+      if (e == cudaSuccess)
+        e = launch_vjp_motion(J.dvol, J.proj, dtype, J.pi, J.grad, J.geom, J.vi, fdk, exact,
+                              J.partials, nullptr, nullptr, br->streams[m]);
+      if (e == cudaSuccess) e = cudaEventRecord(br->joins[m], br->streams[m]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, br->joins[m], 0);
+    }
+  } else {
+    e = launch_batch_vjp(tab, dtype, fdk, exact, s);
+  }
   if (e != cudaSuccess) return e;
   batch_reduce_kernel<<<sms * 8, 256, 0, s>>>(tab);
   if (opt == 1)

@@ -224,19 +224,33 @@ __host__ __device__ inline int batch_find(const int* off, int n, int w) {
 int forward_zb();
 int vjp_view_chunk(const ProjInfo& pi, int dtype, int exact);
 
+// Streams and events for running the members' VJP kernels as parallel
+// branches of a stream capture: fork from the capturing stream, one stream
+// per member, join back.
+struct BatchBranches {
+  int n = 0;  // streams and join events available
+  cudaStream_t* streams = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t* joins = nullptr;
+};
+
 // One iteration of every member: compose -> forward -> loss -> VJP ->
-// reduction and chain -> update, one launch per stage over the table's work
-// items: the forward persistent (SMs x 4 CTAs taking tiles from *counter,
-// which the compose launch resets), the VJP grouped (one block per (tile,
-// view chunk) item), the small stages grid-stride loops.
+// reduction and chain -> update.  Every stage but the VJP is one launch over
+// the table's work items: the forward persistent (SMs x 4 CTAs taking tiles
+// from *counter, which the compose launch resets), the small stages
+// grid-stride loops.  The VJP runs each member's own VJP kernel on its own
+// branch (br, when it has a stream per member), so the members' kernels
+// overlap; without br, one grouped launch (a block per (tile, view chunk)
+// item of every member).
 // loss: 0 sharpness, 1 TV; opt: 0 Eq. 6 step, 1 Adam.
 cudaError_t prepare_batch(int dtype, int fdk, int exact);
 cudaError_t launch_batch_iteration(const BatchTable& tab, unsigned* counter, int dtype, int fdk,
-                                   int exact, int loss, int opt, int sms, cudaStream_t s);
+                                   int exact, int loss, int opt, int sms, cudaStream_t s,
+                                   const BatchBranches* br);
 cudaError_t launch_batch_forward(const BatchTable& tab, unsigned* counter, int dtype, int fdk,
                                  int sms, cudaStream_t s);
 cudaError_t launch_batch_vjp(const BatchTable& tab, int dtype, int fdk, int exact, cudaStream_t s);
-constexpr int BATCH_KERNELS = 7;  // launches per batched iteration
+constexpr int BATCH_KERNELS = 6;  // launches per batched iteration besides the VJP
 
 // Bounds-check word of debug builds (-DBP_BOUNDS_CHECK): op 0 reads the flag
 // bits and the first failure, 1 reads and clears them, 2 records a synthetic

@@ -53,6 +53,10 @@ struct bp_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t last = nullptr;       // after the latest queued step
+  // branches of the VJP stage: a stream and a join event per member
+  std::vector<cudaStream_t> br_streams;
+  std::vector<cudaEvent_t> br_joins;
+  cudaEvent_t br_fork = nullptr;
   struct Retired {                  // graphs of earlier member sets, freed once idle
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -654,10 +658,30 @@ int bp_batch_step(bp_batch* b, int n_iters, void* stream) {
     }
     fill_table(b, b->table);
     e = bpk::prepare_batch(j0->pd.dtype, fdk, exact);
+    if (e == cudaSuccess) e = bpk::prepare_vjp(j0->pd.dtype, fdk, exact);
+    if (e == cudaSuccess && !b->br_fork)
+      e = cudaEventCreateWithFlags(&b->br_fork, cudaEventDisableTiming);
+    while (e == cudaSuccess && b->br_streams.size() < m.size()) {
+      cudaStream_t st = nullptr;
+      cudaEvent_t ev = nullptr;
+      e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (st) b->br_streams.push_back(st);
+      if (ev) b->br_joins.push_back(ev);
+      if (b->br_joins.size() < b->br_streams.size()) {  // keep the two lists paired
+        cudaStreamDestroy(b->br_streams.back());
+        b->br_streams.pop_back();
+      }
+    }
     if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: capture");
+    bpk::BatchBranches br;
+    br.n = (int)b->br_streams.size();
+    br.streams = b->br_streams.data();
+    br.fork = b->br_fork;
+    br.joins = b->br_joins.data();
     const cudaError_t le = bpk::launch_batch_iteration(b->table, b->counter, j0->pd.dtype, fdk,
-                                                       exact, loss, opt, b->sms, b->cap);
+                                                       exact, loss, opt, b->sms, b->cap, &br);
     e = cudaStreamEndCapture(b->cap, &b->graph);
     if (le != cudaSuccess) e = le;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
@@ -678,7 +702,7 @@ int bp_batch_step(bp_batch* b, int n_iters, void* stream) {
     e = cudaGraphLaunch(b->exec, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "bp_batch_step: launch");
   }
-  ctx->launches += (long long)bpk::BATCH_KERNELS * n_iters;
+  ctx->launches += (long long)(bpk::BATCH_KERNELS + (int)m.size()) * n_iters;
   for (bp_job* j : m) {
     j->queued += n_iters;
     e = cudaEventRecord(j->done, s);
@@ -700,6 +724,9 @@ void bp_batch_destroy(bp_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (cudaStream_t st : b->br_streams) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->br_joins) cudaEventDestroy(ev);
+  if (b->br_fork) cudaEventDestroy(b->br_fork);
   if (b->counter) cudaFree(b->counter);
   if (b->last) cudaEventDestroy(b->last);
   delete b;
