@@ -121,7 +121,9 @@ def set_hbm_budget(nbytes, device=None):
 
 class Batch:
     """Resident jobs advanced together (bp_batch_*): every stage of an
-    iteration is one persistent launch over the work items of all members."""
+    iteration but the VJP is one launch over the work items of all members
+    (the backprojection persistent); the members' VJP kernels run as parallel
+    branches of the same captured graph."""
 
     def __init__(self, max_jobs=8, device=None):
         self.ctx = N.context(device)

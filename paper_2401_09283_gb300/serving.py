@@ -3,8 +3,10 @@
 Requests arrive over time (Poisson arrivals).  A request is admitted as soon
 as a slot is free and its device memory fits the HBM budget (the job API's
 admission check); admitted jobs keep all their state on the device and are
-advanced together as one batch: every stage of an iteration is a single
-persistent launch over the work items of all resident jobs (bp_batch_step).
+advanced together as one batch (bp_batch_step): compose, backprojection,
+loss, reduction and update are each a single launch over the work items of
+all resident jobs (the backprojection persistent), and the jobs' motion VJPs
+run as parallel branches of the same graph.
 A finished job is read back and freed with the stream-ordered allocator (no
 device-wide synchronisation), and the next waiting request takes its slot.
 
@@ -136,8 +138,9 @@ class Server:
     admission by free HBM (or an explicit budget), FIFO.
 
     batched=True (the serving form): the resident jobs are the members of one
-    bp_batch, and every stage of an iteration is ONE persistent launch over
-    the work items of all of them (bp_batch_step replays one captured graph).
+    bp_batch; every stage of an iteration but the VJP is ONE launch over the
+    work items of all of them, the VJPs run as parallel graph branches
+    (bp_batch_step replays one captured graph).
     The batch advances in steps of at most `chunk` iterations, never past a
     member's remaining iterations; a job that finishes leaves the batch and
     the next waiting request takes its slot at the following step.  Two steps
