@@ -269,13 +269,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": cfg.name, "volume": list(cfg.vol_shape),
-                      "voxel_mm": cfg.spacing, "views": V, "detector": [cfg.nv, cfg.nu],
-                      "weight": "fdk", "deriv": "central",
-                      "updates_per_step": "3*N^3*V (forward, motion VJP, data VJP)",
-                      "l2": "inputs larger than L2 (projections %.0f MB + volumes %.0f MB)"
-                            % (proj.numel() * 4 / 1e6, 2 * vol.numel() * 4 / 1e6),
-                      "parallelism": "replicas" if ws > 1 else "single"},
+           "config": workload_config(cfg, ws),
            "gpu_launches": launches, "roofline": roof, "kernels": kernels,
            "loss_last": float(loss)}
     if clk:
@@ -593,6 +587,17 @@ def cpu_baseline(cfg, P, proj, seconds):
     return out
 
 
+def workload_config(cfg, ws):
+    """The `config` of both arms' JSON lines."""
+    proj_mb = cfg.views * cfg.nv * cfg.nu * 4 / 1e6
+    vol_mb = 2 * cfg.voxels * 4 / 1e6
+    return {"workload": cfg.name, "volume": list(cfg.vol_shape), "voxel_mm": cfg.spacing,
+            "views": cfg.views, "detector": [cfg.nv, cfg.nu], "weight": "fdk", "deriv": "central",
+            "updates_per_step": "3*N^3*V (forward, motion VJP, data VJP)",
+            "l2": "inputs larger than L2 (projections %.0f MB + volumes %.0f MB)" % (proj_mb, vol_mb),
+            "parallelism": "replicas" if ws > 1 else "single"}
+
+
 def run_reference(args):
     """The oracle as the reference arm, on the host cores of rank 0."""
     ws, rank, local = dist_env()
@@ -630,8 +635,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": cfg.name, "volume": list(cfg.vol_shape), "views": cfg.views,
-                      "detector": [cfg.nv, cfg.nu], "weight": "fdk", "deriv": "central"},
+           "config": workload_config(cfg, ws),
            "cpu_baseline": res,
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}

@@ -1531,8 +1531,9 @@ __global__ void __launch_bounds__(NT, VJP_MINB)
 #endif
 // Views per chunk of the view-chunked VJP grids: the bytes that one chunk's
 // views touch (projections, gradient images, dL/dproj rows) are kept near
-// BP_VJP_CHUNK_MIB, at most 32 views.  Measured on c2 (fused VJP): 16 MiB
-// 23.1 ms, 32 MiB 20.3 ms, 64 MiB 18.1 ms, 128 MiB 17.4 ms.
+// BP_VJP_CHUNK_MIB, at most 32 views.  Measured on c2 (fused VJP, before
+// the block image): 16 MiB 23.1 ms, 32 MiB 20.3 ms, 64 MiB 18.1 ms, 128 MiB
+// 17.4 ms.
 static int view_chunk(const ProjInfo& pi, long long bytes_per_px) {
   const long long per_view = (long long)pi.nu * pi.nv * bytes_per_px;
   long long c = ((long long)BP_VJP_CHUNK_MIB << 20) / (per_view > 0 ? per_view : 1);
@@ -1564,8 +1565,10 @@ static cudaError_t vjp_dispatch(const float* dvol, const void* proj, const ProjI
   const bool stage = stageable<T>(proj, pi);
   // block images only where the staged CENTRAL paths scatter
   const bool useb = dproj && blk && stage && !EXACT && BP_VJP_BLOCKS;
-  const long long bpp =
-      (long long)sizeof(T) + (EXACT ? 0 : 8) + (dproj ? 4 : 0) + (useb ? 16 : 0);
+  // the block image is left out of the chunk's byte count: measured on c2,
+  // counting its 16 bytes per pixel (smaller chunks) made the fused VJP 2.8 %
+  // slower (15.37 against 14.94 ms), counting 8 bytes 1.7 %
+  const long long bpp = (long long)sizeof(T) + (EXACT ? 0 : 8) + (dproj ? 4 : 0);
   const int vc = view_chunk(pi, bpp);
   const unsigned nblocks = (unsigned)((long long)ntiles * ((pi.nviews + vc - 1) / vc));
   if (dproj) {
