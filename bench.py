@@ -50,9 +50,12 @@ PASS_COST = {
 # DRAM bytes (read + write) per launch of each kernel on the c2 workload:
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
 # current kernels at full c2 size (one launch each; the capture and its
-# command are kept with the profiles).  Reported as the roofline's "traffic"
-# for c2 only; it must be re-captured whenever one of these kernels changes.
-NCU_TRAFFIC_C2 = {"forward": 0.4700e9, "vjp_fused": 1.7366e9, "vjp_motion": 1.1013e9}
+# command are kept with the profiles).  "vjp_fused" is the fused VJP kernel
+# plus the block-image combine kernel (3.644e9 + 1.747e9); the block image's
+# memset (1.17 GB written) is not a kernel of ours and not included.
+# Reported as the roofline's "traffic" for c2 only; it must be re-captured
+# whenever one of these kernels changes.
+NCU_TRAFFIC_C2 = {"forward": 0.4639e9, "vjp_fused": 5.3908e9}
 
 
 def parse():
@@ -255,7 +258,8 @@ def run_ours(args):
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak / 1e9,
             "unit": "Gupdate/s", "frac": achieved / peak,
             "traffic": NCU_TRAFFIC_C2.get(dom) if cfg.name == W.C2.name else None,
-            "traffic_unit": "bytes per launch (ncu dram__bytes_read+write)",
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read+write; vjp_fused: VJP "
+                            "kernel + block-image combine)",
             "peak_basis": "min(FP32 issue %.0f, LSU %.0f) Gupdate/s at %d SMs x %.0f MHz"
                           % (r_fp32 / 1e9, r_lsu / 1e9, sms, SM_MAX_MHZ)}
     kernels = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else None, "launches": v[1],
