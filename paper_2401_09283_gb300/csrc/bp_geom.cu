@@ -213,26 +213,29 @@ __device__ static void sharpness_block(const float* __restrict__ vol, int nx, in
   const long long nxy = (long long)nx * ny;
   for (long long x = b * (long long)SH_THREADS + threadIdx.x; x < nvox;
        x += (long long)nb * SH_THREADS) {
-    int i = (int)(x % nx);
-    int j = (int)((x / nx) % ny);
-    int k = (int)(x / nxy);
+    int i, j, k;
+    voxel_ijk(x, nx, ny, nvox, i, j, k);
     float c = vol[x];
     float gsum = 0.0f;
+    // the voxel's squared forward differences summed in FP32 (x, y, z order),
+    // accumulated in FP64: one FP64 add per voxel (FP64 is slow on GB300)
+    float q = 0.0f;
     if (i + 1 < nx) {
       float d = vol[x + 1] - c;
-      acc += (double)d * d;
+      q = d * d;
       gsum += d;
     }
     if (j + 1 < ny) {
       float d = vol[x + nx] - c;
-      acc += (double)d * d;
+      q = fmaf(d, d, q);
       gsum += d;
     }
     if (k + 1 < nz) {
       float d = vol[x + nxy] - c;
-      acc += (double)d * d;
+      q = fmaf(d, d, q);
       gsum += d;
     }
+    acc += (double)q;
     if (grad) {
       if (i > 0) gsum += vol[x - 1] - c;
       if (j > 0) gsum += vol[x - nx] - c;
@@ -481,7 +484,8 @@ __device__ static void tv_block(const float* __restrict__ vol, int nx, int ny, i
   double acc = 0.0;
   for (long long x = b * (long long)SH_THREADS + threadIdx.x; x < nvox;
        x += (long long)nb * SH_THREADS) {
-    const int i = (int)(x % nx), j = (int)((x / nx) % ny), k = (int)(x / nxy);
+    int i, j, k;
+    voxel_ijk(x, nx, ny, nvox, i, j, k);
     float gsum = 0.0f, gx, gy, gz, in;
     double n;
     if (tv_interior(i, j, k, nx, ny, nz)) {

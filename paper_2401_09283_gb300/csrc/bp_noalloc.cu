@@ -48,24 +48,31 @@ __global__ void sharp_chunk_kernel(const float* __restrict__ vol, int nx, int ny
   for (int r = 0; r < NA_PER_THREAD; ++r) {
     const long long x = base + (long long)r * NA_THREADS + threadIdx.x;
     if (x >= nvox) break;
-    const int i = (int)(x % nx), j = (int)((x / nx) % ny), k = (int)(x / nxy);
+    // nvox <= 512^3 < 2^32: 32-bit index arithmetic
+    const unsigned ux = (unsigned)x, qx = ux / (unsigned)nx;
+    const int i = (int)(ux - qx * (unsigned)nx), j = (int)(qx % (unsigned)ny),
+              k = (int)(qx / (unsigned)ny);
     const float c = vol[x];
     float gsum = 0.0f;
+    // the voxel's squared forward differences summed in FP32 (x, y, z order),
+    // accumulated in FP64 -- the per-voxel arithmetic of bp_sharpness
+    float q = 0.0f;
     if (i + 1 < nx) {
       const float d = vol[x + 1] - c;
-      acc += (double)d * d;
+      q = d * d;
       gsum += d;
     }
     if (j + 1 < ny) {
       const float d = vol[x + nx] - c;
-      acc += (double)d * d;
+      q = fmaf(d, d, q);
       gsum += d;
     }
     if (k + 1 < nz) {
       const float d = vol[x + nxy] - c;
-      acc += (double)d * d;
+      q = fmaf(d, d, q);
       gsum += d;
     }
+    acc += (double)q;
     if (grad) {
       if (i > 0) gsum += vol[x - 1] - c;
       if (j > 0) gsum += vol[x - nx] - c;

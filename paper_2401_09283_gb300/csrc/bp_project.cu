@@ -803,15 +803,15 @@ cudaError_t launch_forward(const void* proj, int dtype, const ProjInfo& pi, cons
 // stored units (the per-view dequantisation scale is applied with the view
 // weight); output contiguous [V][nv][nu] float2.
 template <typename T>
-__global__ void grad_images_kernel(const T* __restrict__ proj, ProjInfo pi,
-                                   float2* __restrict__ grad) {
-  const long long n = (long long)pi.nviews * pi.nv * pi.nu;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int a = (int)(e % pi.nu);
-    const int b = (int)((e / pi.nu) % pi.nv);
-    const int j = (int)(e / ((long long)pi.nu * pi.nv));
-    const T* row = proj + (long long)j * pi.vs + (long long)b * pi.rs;
+__global__ void __launch_bounds__(256) grad_images_kernel(const T* __restrict__ proj, ProjInfo pi,
+                                                         float2* __restrict__ grad) {
+  // one CTA per detector row (view j, row b); consecutive threads take
+  // consecutive columns
+  const long long rowi = blockIdx.x;
+  const int j = (int)(rowi / pi.nv), b = (int)(rowi - (long long)j * pi.nv);
+  const T* row = proj + (long long)j * pi.vs + (long long)b * pi.rs;
+  float2* out = grad + rowi * pi.nu;
+  for (int a = threadIdx.x; a < pi.nu; a += blockDim.x) {
     float gu = 0.0f, gv = 0.0f;
     if (pi.nu >= 2) {
       if (a == 0) gu = ldv(row + 1) - ldv(row);
@@ -823,16 +823,15 @@ __global__ void grad_images_kernel(const T* __restrict__ proj, ProjInfo pi,
       else if (b == pi.nv - 1) gv = ldv(row + a) - ldv(row - pi.rs + a);
       else gv = 0.5f * (ldv(row + pi.rs + a) - ldv(row - pi.rs + a));
     }
-    grad[e] = make_float2(gu, gv);
+    out[a] = make_float2(gu, gv);
   }
 }
 
 cudaError_t launch_grad_images(const void* proj, int dtype, const ProjInfo& pi, float2* grad,
                                cudaStream_t s) {
-  const long long n = (long long)pi.nviews * pi.nv * pi.nu;
-  if (n == 0) return cudaSuccess;
-  long long nb = (n + 255) / 256;
-  if (nb > 152 * 64) nb = 152 * 64;
+  const long long nb = (long long)pi.nviews * pi.nv;  // detector rows
+  if (nb == 0 || pi.nu == 0) return cudaSuccess;
+  if (nb > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (dtype == 0)
     grad_images_kernel<float><<<(int)nb, 256, 0, s>>>((const float*)proj, pi, grad);
   else if (dtype == 1)
