@@ -806,7 +806,9 @@ template <typename T>
 __global__ void __launch_bounds__(256) grad_images_kernel(const T* __restrict__ proj, ProjInfo pi,
                                                          float2* __restrict__ grad) {
   // one CTA per detector row (view j, row b); consecutive threads take
-  // consecutive columns
+  // consecutive columns (measured on c2: 0.29 ms against 0.37 ms for a flat
+  // grid-stride loop with 64-bit index divisions, 0.30 ms for CTAs looping
+  // over rows)
   const long long rowi = blockIdx.x;
   const int j = (int)(rowi / pi.nv), b = (int)(rowi - (long long)j * pi.nv);
   const T* row = proj + (long long)j * pi.vs + (long long)b * pi.rs;
