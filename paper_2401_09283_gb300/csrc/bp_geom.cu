@@ -643,9 +643,10 @@ cudaError_t launch_batch_iteration(const BatchTable& tab, unsigned* counter, int
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (br && tab.njobs > 0 && br->n >= tab.njobs) {
+  if (tab.njobs > 0) {
     // each member's VJP kernel (the per-job launch, with its own constant
     // parameters) on a branch of its own
+    if (!br || br->n < tab.njobs) return cudaErrorInvalidValue;
     e = cudaEventRecord(br->fork, s);
     for (int m = 0; m < tab.njobs && e == cudaSuccess; ++m) {
       const BatchJob& J = tab.job[m];
@@ -656,8 +657,6 @@ cudaError_t launch_batch_iteration(const BatchTable& tab, unsigned* counter, int
       if (e == cudaSuccess) e = cudaEventRecord(br->joins[m], br->streams[m]);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(s, br->joins[m], 0);
     }
-  } else {
-    e = launch_batch_vjp(tab, dtype, fdk, exact, s);
   }
   if (e != cudaSuccess) return e;
   batch_reduce_kernel<<<sms * 8, 256, 0, s>>>(tab);

@@ -196,7 +196,7 @@ struct BatchJob {
   double sid;
   double lr_t, lr_r, beta1, beta2, eps, decay;
   float tv_eps;
-  int V, ntiles_f, ntiles_v, vchunk, nblk, max_iters, gauge;
+  int V, ntiles_f, ntiles_v, nblk, max_iters, gauge;
 };
 
 struct BatchTable {
@@ -204,7 +204,6 @@ struct BatchTable {
   int off_view[BATCH_MAX_JOBS + 1];  // prefix sums of V (compose, reduction)
   int off_fwd[BATCH_MAX_JOBS + 1];   // of forward tiles
   int off_loss[BATCH_MAX_JOBS + 1];  // of loss blocks
-  int off_vjp[BATCH_MAX_JOBS + 1];   // of VJP (tile, view chunk) items
   BatchJob job[BATCH_MAX_JOBS];
 };
 static_assert(sizeof(BatchTable) <= 30000, "the member table must fit the kernel parameters");
@@ -240,7 +239,6 @@ __host__ __device__ inline int batch_find(const int* off, int n, int w) {
 
 // Forward tiling and VJP view chunk of a job (host side, for the table).
 int forward_zb();
-int vjp_view_chunk(const ProjInfo& pi, int dtype, int exact);
 
 // Streams and events for running the members' VJP kernels as parallel
 // branches of a stream capture: fork from the capturing stream, one stream
@@ -257,9 +255,8 @@ struct BatchBranches {
 // the table's work items: the forward persistent (SMs x 4 CTAs taking tiles
 // from *counter, which the compose launch resets), the small stages
 // grid-stride loops.  The VJP runs each member's own VJP kernel on its own
-// branch (br, when it has a stream per member), so the members' kernels
-// overlap; without br, one grouped launch (a block per (tile, view chunk)
-// item of every member).
+// branch, so the members' kernels overlap: br must hold a stream and a join
+// event per member (cudaErrorInvalidValue otherwise).
 // loss: 0 sharpness, 1 TV; opt: 0 Eq. 6 step, 1 Adam.
 cudaError_t prepare_batch(int dtype, int fdk, int exact);
 cudaError_t launch_batch_iteration(const BatchTable& tab, unsigned* counter, int dtype, int fdk,
@@ -267,7 +264,6 @@ cudaError_t launch_batch_iteration(const BatchTable& tab, unsigned* counter, int
                                    const BatchBranches* br);
 cudaError_t launch_batch_forward(const BatchTable& tab, unsigned* counter, int dtype, int fdk,
                                  int sms, cudaStream_t s);
-cudaError_t launch_batch_vjp(const BatchTable& tab, int dtype, int fdk, int exact, cudaStream_t s);
 constexpr int BATCH_KERNELS = 6;  // launches per batched iteration besides the VJP
 
 // Bounds-check word of debug builds (-DBP_BOUNDS_CHECK): op 0 reads the flag

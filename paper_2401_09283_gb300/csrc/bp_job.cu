@@ -488,7 +488,7 @@ bool same_config(const bp_job* a, const bp_job* b) {
 void fill_table(bp_batch* b, bpk::BatchTable& T) {
   const int n = (int)b->members.size();
   T.njobs = n;
-  T.off_view[0] = T.off_fwd[0] = T.off_loss[0] = T.off_vjp[0] = 0;
+  T.off_view[0] = T.off_fwd[0] = T.off_loss[0] = 0;
   const int zbf = bpk::forward_zb();
   for (int k = 0; k < n; ++k) {
     const bp_job* j = b->members[k];
@@ -525,15 +525,12 @@ void fill_table(bp_batch* b, bpk::BatchTable& T) {
     J.V = j->pd.nviews;
     J.ntiles_f = J.vif.tiles_x * J.vif.tiles_y * J.vif.tiles_z;
     J.ntiles_v = j->ntiles;
-    J.vchunk = bpk::vjp_view_chunk(j->pi, j->pd.dtype, j->deriv == BP_DERIV_BILINEAR_EXACT);
     J.nblk = j->nblk;
     J.max_iters = j->max_iters;
     J.gauge = j->opt.gauge;
-    const int nchunks = (J.V + J.vchunk - 1) / J.vchunk;
     T.off_view[k + 1] = T.off_view[k] + J.V;
     T.off_fwd[k + 1] = T.off_fwd[k] + J.ntiles_f;
     T.off_loss[k + 1] = T.off_loss[k] + J.nblk;
-    T.off_vjp[k + 1] = T.off_vjp[k] + J.ntiles_v * nchunks;
   }
 }
 
