@@ -363,7 +363,8 @@ def motion_estimation_leg(args, cfg, P, th_true, proj, vw, dev):
 def serving_leg(args, device):
     """Config 5: a seeded Poisson stream of motion-estimation jobs (volumes
     128-384^3, 120-496 views, 50 iterations each) served with FP16
-    projections as one batch of resident jobs (batched persistent launches),
+    projections by batches of resident jobs (two batch lanes: small and large
+    jobs on priority streams),
     against the same jobs one at a time in plain FP32; jobs/s, p50/p99
     latency and the final reprojection error of each form, best of
     `serving_repeats` runs with every run's jobs/s listed, plus one run of the

@@ -137,14 +137,18 @@ class Server:
     """Continuous-batching server: up to `slots` jobs resident at once,
     admission by free HBM (or an explicit budget), FIFO.
 
-    batched=True (the serving form): the resident jobs are the members of one
-    bp_batch; every stage of an iteration but the VJP is ONE launch over the
-    work items of all of them, the VJPs run as parallel graph branches
-    (bp_batch_step replays one captured graph).
-    The batch advances in steps of at most `chunk` iterations, never past a
-    member's remaining iterations; a job that finishes leaves the batch and
-    the next waiting request takes its slot at the following step.  Two steps
-    are kept queued on the device, so admissions and read-backs on the host
+    batched=True (the serving form): the resident jobs are the members of
+    `lanes` bp_batches -- with two lanes, jobs of at most `small_voxel_views`
+    voxel-views per iteration in a batch on a high-priority stream, larger ones
+    in a batch on a low-priority stream, so that small jobs do not advance in
+    lockstep with large ones and the two batches fill each other's kernel
+    tails.  In a batch every stage of an iteration but the VJP is ONE launch
+    over the work items of all its members, the VJPs run as parallel graph
+    branches (bp_batch_step replays one captured graph).  A batch advances in
+    steps of at most `chunk` iterations, never past a member's remaining
+    iterations; a job that finishes leaves its batch and the next waiting
+    request takes its slot at the following step.  Two steps per batch are
+    kept queued on the device, so admissions and read-backs on the host
     overlap the GPU's work.
 
     batched=False: each resident job replays its own iteration graph
@@ -157,9 +161,11 @@ class Server:
     cancels a waiting or resident job.  Every result carries its status."""
 
     def __init__(self, device=0, slots=4, opt: OptConfig = OptConfig(), hbm_budget=0, chunk=5,
-                 batched=True, deadline_s=None):
+                 batched=True, deadline_s=None, lanes=2, small_voxel_views=2 ** 31):
         self.device = device
         self.slots = slots
+        self.lanes = lanes
+        self.small_voxel_views = small_voxel_views
         self.opt = opt
         self.hbm_budget = hbm_budget
         self.chunk = chunk
@@ -248,16 +254,24 @@ class Server:
                 r.rpe = _rpe(by_id[r.job_id], r.theta, self.device)
         return sorted(results, key=lambda r: r.job_id)
 
+    def _lane_of(self, req):
+        """Batch lane of a request: 0 (high-priority stream) for jobs of at
+        most `small_voxel_views` voxel-views per iteration, else 1."""
+        if self.lanes < 2:
+            return 0
+        return 0 if req.cfg.voxel_views <= self.small_voxel_views else 1
+
     def _run_batched(self, requests, dev):
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting = collections.deque()
-        active = []   # admission order: dicts req, job, left, admitted, status
-        done = collections.deque()  # finished jobs whose last iterations may still be queued
+        active = []   # admission order: dicts req, job, left, admitted, status, lane
+        done = []     # finished jobs whose last iterations may still be queued
         results = []
-        batch = Batch(max_jobs=self.slots, device=self.device)
-        stream = torch.cuda.Stream(dev)
-        inflight = collections.deque()  # events of the queued steps
-        members = []
+        least, greatest = torch.cuda.Stream.priority_range()
+        lanes = [dict(batch=Batch(max_jobs=self.slots, device=self.device),
+                      stream=torch.cuda.Stream(dev, priority=min(greatest + k, least)),
+                      inflight=collections.deque(), members=[])
+                 for k in range(max(1, self.lanes))]
         t0 = time.perf_counter()
         try:
             while pending or waiting or active or done:
@@ -265,39 +279,53 @@ class Server:
                 while pending and pending[0].arrival <= now:
                     waiting.append(pending.popleft())
                 self._expire(active, t0)
-                # finished (or cancelled) jobs leave the batch and free their slot
+                # finished (or cancelled) jobs leave their batch and free their slot
                 done.extend(a for a in active if a["left"] == 0)
                 active = [a for a in active if a["left"] > 0]
+                n_before = len(active)
                 self._admit(waiting, active, results, t0)
-                running = active
-                if [a["job"] for a in running] != members:
-                    members = [a["job"] for a in running]
-                    batch.set_jobs(members)
-                if running:
-                    n = min(self.chunk, min(a["left"] for a in running))
-                    batch.step(n, stream.cuda_stream)
-                    self.steps += 1
-                    ev = torch.cuda.Event()
-                    ev.record(stream)
-                    inflight.append(ev)
-                    for a in running:
-                        a["left"] -= n
-                # read back the jobs whose last step has run; keep two steps queued
-                while done and done[0]["job"].wait(0.0):
-                    self._finish(done.popleft(), results, t0)
-                while len(inflight) > 2 or (inflight and not running):
-                    inflight.popleft().synchronize()
-                    while done and done[0]["job"].wait(0.0):
-                        self._finish(done.popleft(), results, t0)
-                if not running and not done and not waiting and pending:
+                for a in active[n_before:]:
+                    a["lane"] = self._lane_of(a["req"])
+                progressed = False
+                for k, L in enumerate(lanes):
+                    while L["inflight"] and L["inflight"][0].query():
+                        L["inflight"].popleft()
+                    running = [a for a in active if a["lane"] == k]
+                    jobs = [a["job"] for a in running]
+                    if jobs != L["members"]:
+                        L["members"] = jobs
+                        L["batch"].set_jobs(jobs)
+                    # keep two steps of each lane queued on the device, so
+                    # admissions and read-backs on the host overlap its work
+                    if running and len(L["inflight"]) < 2:
+                        n = min(self.chunk, min(a["left"] for a in running))
+                        L["batch"].step(n, L["stream"].cuda_stream)
+                        self.steps += 1
+                        ev = torch.cuda.Event()
+                        ev.record(L["stream"])
+                        L["inflight"].append(ev)
+                        for a in running:
+                            a["left"] -= n
+                        progressed = True
+                # read back the jobs whose last step has run
+                for a in [a for a in done if a["job"].wait(0.0)]:
+                    done.remove(a)
+                    self._finish(a, results, t0)
+                    progressed = True
+                if progressed:
+                    continue
+                if not active and not done and not waiting and pending:
                     time.sleep(max(0.0, min(0.005, pending[0].arrival - (time.perf_counter() - t0))))
-                elif not running and done:
+                elif not active and done and not waiting:
                     for a in list(done):
                         a["job"].wait(-1.0)
                         self._finish(a, results, t0)
                     done.clear()
+                else:
+                    time.sleep(0.0002)
         finally:
-            batch.close()
+            for L in lanes:
+                L["batch"].close()
         return results
 
     def _run_streams(self, requests, dev):
@@ -372,7 +400,7 @@ def _moved(req: Request):
 
 def compare(n_jobs=16, rate=4.0, seed=5, slots=4, opt: OptConfig = OptConfig(), repeats=1,
             sizes=(128, 192, 256, 384), views=(120, 248, 496), device=0, streams_form=True):
-    """The served FP16 form (batched persistent launches) against the same
+    """The served FP16 form (batched launches in two lanes) against the same
     requests served one at a time in plain FP32, `repeats` runs of each (the
     spread of jobs/s), plus one run of the served FP16 form without batching
     (per-job graphs on streams) when streams_form is set."""
@@ -433,7 +461,8 @@ def summarize(results, requests, server):
     if server is not None:
         out["max_concurrent_jobs"] = server.max_concurrent
         out["max_resident_gb"] = server.max_resident_bytes / 1e9
-        out["form"] = "batched persistent launches" if server.batched else "per-job graphs on streams"
+        out["form"] = ("batched launches, %d batch lane(s) on priority streams" % server.lanes
+                       if server.batched else "per-job graphs on streams")
     return out
 
 
