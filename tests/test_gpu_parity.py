@@ -1,8 +1,7 @@
 """GPU parity: the CUDA path through the C-ABI against the FP64 oracle on the
 same seeded inputs.
 
-Tolerances (stated by the benchmark spec, or derived in the design
-notes): volumes rel-L2 <= 1e-5 for FP32 data; motion gradients rel-L2
+Tolerances: volumes rel-L2 <= 1e-5 for FP32 data; motion gradients rel-L2
 <= 1e-3 per parameter group (translations, rotations); FP16-stored data
 rel-L2 <= 2e-3 against the oracle on the FP32 data; BF16 <= 2^-9, its unit
 roundoff (derivation beside BF16_STORAGE_TOL in cases.py).
