@@ -168,10 +168,11 @@ int bp_forward(bp_ctx* ctx, const void* proj, const bp_proj_desc* pdesc, const d
  *               gradient with respect to Phat_j = P_j T(motion_j);
  *   dL_dproj    float32 [V][nv][nu] (contiguous): the adjoint of Eq. 3 in
  *               the data, overwritten (FP32 atomics: not bitwise
- *               deterministic).  With 16-byte aligned detector rows the
- *               context holds a scratch block image of 16 bytes per detector
- *               pixel of every view for it (4x the size of dL_dproj; see
- *               bp_ctx_workspace_bytes), kept between calls.
+ *               deterministic).  The context holds a scratch block image
+ *               of 16 bytes per detector pixel of every view for it (4x the
+ *               size of dL_dproj; see bp_ctx_workspace_bytes), kept between
+ *               calls -- when dL_dproj comes with the motion gradients, only
+ *               for projections with 16-byte aligned rows.
  * Any output may be NULL to skip it (dL_dmotion needs motion or treats it as
  * zero).  With BP_WEIGHT_FDK the derivative of (sid/w)^2 is included. */
 int bp_vjp(bp_ctx* ctx, const float* dL_dvol, const void* proj, const bp_proj_desc* pdesc,
